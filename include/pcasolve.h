@@ -1,0 +1,153 @@
+/*
+ * pcasolve.h -- C ABI of the GB300 (sm_103a) single-projection PCA lung-motion
+ * solver: Li et al., "3D tumor localization through real-time volumetric x-ray
+ * imaging for lung cancer radiotherapy", arXiv:1102.1712.
+ *
+ * The method (Sec. II.A and Appendix): a reference CT f0 is deformed by the
+ * PCA motion model x = xbar + U w (Eq. 1), projected to a digitally
+ * reconstructed radiograph P f, and w is fitted to one measured cone-beam
+ * projection y by minimising J = ||P f - a y - b||^2 (Eq. 2), alternating the
+ * intensity fit (Eq. A.1) with normalised gradient steps under Armijo
+ * backtracking (Eq. A.2).  The tumour is then located by inverting the DVF at
+ * its reference centroid (Sec. II.A, fixed point of Chen et al.).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Memory.  Pointers documented "device" are CUDA device pointers owned by the
+ *   caller; pointers documented "host" are ordinary host memory.  No call
+ *   allocates device memory: calls that need scratch take a caller-provided
+ *   device workspace sized by pcas_workspace_bytes().
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Calls whose outputs are device arrays only enqueue work and
+ *   return; calls with host outputs (marked "synchronous") block until those
+ *   outputs are ready.
+ * Volumes.  float32, layout [nz][ny][nx] (x fastest), voxel (i,j,k) centred
+ *   at (ox + i sx, oy + j sy, oz + k sz) mm.  Values outside the grid are 0.
+ * Motion model.  mean: [3][N] float32 mm (may be NULL = zero mean field);
+ *   U: [K][3][N] float32 mm, component 0 = x (lateral), 1 = y (AP),
+ *   2 = z (SI), N = nx ny nz; 1 <= K <= PCAS_KMAX.
+ * Images.  float32, layout [nv][nu] (u fastest).
+ * Geometry (a reading; the paper does not state axes).  Gantry rotation about
+ *   z through the world origin; source S = (sad sin a, -sad cos a, 0); the
+ *   detector plane is normal to the central ray at distance sdd from S; pixel
+ *   (iu,iv) centre = S + sdd ew + ((iu - (nu-1)/2) du + off_u) eu
+ *   + ((iv - (nv-1)/2) dv + off_v) ev, ew = (-sin a, cos a, 0),
+ *   eu = (cos a, sin a, 0), ev = (0, 0, 1).  The whole support box of the
+ *   volume must lie in front of the source (else PCAS_ERR_INVALID_ARG).
+ * Projector P (a reading; the paper only says P projects f, Eq. 2).  Pixel
+ *   value = step * sum_i f(S + i step dhat) over the integers i whose sample
+ *   lies in the support box [-1, n_c] (voxel units) of the trilinear
+ *   interpolant (Eq. A.5): a source-anchored ray march, so P and P^T visit
+ *   exactly the same (ray, sample) pairs.
+ * Errors.  Every call returns a pcas_status; pcas_last_error() returns a
+ *   message for the calling thread's last failure.  Arguments are checked
+ *   before any work is enqueued; a failed check leaves outputs untouched.
+ */
+#ifndef PCASOLVE_H
+#define PCASOLVE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PCAS_KMAX 8
+#define PCAS_VERSION 1
+
+typedef enum {
+    PCAS_OK = 0,
+    PCAS_ERR_INVALID_ARG = 1,   /* bad pointer, size, geometry or workspace   */
+    PCAS_ERR_SINGULAR = 2,      /* Y^T Y of Eq. (A.1) singular (constant y)   */
+    PCAS_ERR_CUDA = 3,          /* a CUDA runtime call or launch failed        */
+    PCAS_NOT_CONVERGED = 4,     /* informational: iteration cap reached        */
+    PCAS_ERR_TIMEOUT = 5        /* reserved: bounded device wait expired       */
+} pcas_status;
+
+typedef struct { int nx, ny, nz; double sx, sy, sz, ox, oy, oz; } pcas_vol;
+typedef struct { double sad, sdd; int nu, nv; double du, dv, off_u, off_v, angle_rad; } pcas_cb;
+
+/* Appendix, after Eq. (A.2): mu0 = 2, alpha = 0.1, beta = 0.5, stop when mu
+ * < 0.1 or after 10 iterations, for w preconditioned to standard deviation
+ * 10.  For O(1) coefficients use mu0 = 0.2, mu_min = 0.01.  max_trials caps
+ * the backtracking steps of one iteration; step_mm is the ray-march step. */
+typedef struct { double mu0, alpha, beta, mu_min; int max_iter, max_trials; double step_mm; } pcas_params;
+
+/* iters: completed iterations; evals: DRR evaluations (1 + trials);
+ * J0: cost at the first iteration; J, a, b: cost and intensity scaling at the
+ * end; mu_last: last step size tried; status: pcas_status of the solve. */
+typedef struct { int iters, evals, status; double J0, J, a, b, mu_last; } pcas_stats;
+
+const char* pcas_last_error(void);
+int pcas_version(void);
+
+/* Bytes of device workspace needed by cost_grad / solve_projection for this
+ * volume, view and K (0 if the arguments are invalid).  Pass a 256-byte
+ * aligned buffer of at least this size. */
+size_t pcas_workspace_bytes(const pcas_vol* vol, const pcas_cb* cb, int K);
+
+/* Eq. (1): dvf[c][v] = mean[c][v] + sum_k w[k] U[k][c][v].
+ * mean, U, dvf: device; w: host, K doubles.  Asynchronous. */
+int pca_dvf(const float* mean, const float* U, int K, const double* w, const pcas_vol* vol,
+            float* dvf, void* stream);
+
+/* Eq. (A.3)/(A.5): f(i,j,k) = f0 trilinearly sampled at
+ * (i + dvf[0]/sx, j + dvf[1]/sy, k + dvf[2]/sz), zero outside the grid.
+ * f0, dvf ([3][N] mm), f: device.  Asynchronous. */
+int warp_volume(const float* f0, const float* dvf, const pcas_vol* vol, float* f, void* stream);
+
+/* Eq. (2), the projector P: p = P f (definition in the header comment).
+ * f, p: device.  step_mm > 0.  Asynchronous. */
+int drr_forward(const float* f, const pcas_vol* vol, const pcas_cb* cb, double step_mm,
+                float* p, void* stream);
+
+/* P^T, the exact transpose of drr_forward (gradient formula below Eq. A.2),
+ * computed in gather form without atomics: g[v] = step sum over rays and
+ * samples of img(ray) times the trilinear weight of voxel v.
+ * img, g: device; g is overwritten.  Asynchronous. */
+int drr_adjoint(const float* img, const pcas_vol* vol, const pcas_cb* cb, double step_mm,
+                float* g, void* stream);
+
+/* One evaluation at w: (a, b) by Eq. (A.1) on P f(w), J by Eq. (2) and
+ * dJ/dw = 2 U^T (df/dx) P^T (P f - a y - b) (gradient below Eq. A.2, warp
+ * Jacobian of Eq. A.8) with (a, b) held.  f0, mean, U, y, ws: device;
+ * w (K), J (1), dJdw (K), ab (2): host.  Synchronous.
+ * Returns PCAS_ERR_SINGULAR if y is constant. */
+int cost_grad(const float* f0, const float* mean, const float* U, int K, const double* w,
+              const float* y, const pcas_vol* vol, const pcas_cb* cb, double step_mm,
+              double* J, double* dJdw, double* ab, void* ws, size_t ws_bytes, void* stream);
+
+/* Appendix: alternate Eq. (A.1) and Eq. (A.2) from w_init.  Each iteration
+ * refits (a, b), takes d = -G/||G|| and tries mu = mu0, beta mu0, ... while
+ * mu >= mu_min and at most max_trials times, accepting the first mu with
+ * J(w + mu d) <= J(w) - alpha mu ||G||; if none passes, no step is taken and
+ * the solve ends.  It also ends after max_iter iterations or at G = 0.
+ * f0, mean, U, y, ws: device; w_init, w_out (K), params, stats: host.
+ * Synchronous (one host read of a 4-byte flag per trial step). */
+int solve_projection(const float* f0, const float* mean, const float* U, int K, const float* y,
+                     const pcas_vol* vol, const pcas_cb* cb, const double* w_init,
+                     const pcas_params* params, double* w_out, pcas_stats* stats, void* ws,
+                     size_t ws_bytes, void* stream);
+
+/* Sec. II.A: the DVF is a pull-back field (new-image point c maps to
+ * c + x(c) in the reference), so the tumour position solves c + x(c) = c_ref;
+ * iterate y <- -x(c_ref + y) from y = 0 (x trilinear in mm, zero outside the
+ * grid) until the update is below tol_mm or max_iter is reached; c = c_ref + y.
+ * mean, U: device; w (K), c_ref, c_out: host.  Synchronous.  Returns
+ * PCAS_NOT_CONVERGED (with c_out set) if the cap was reached. */
+int localize_tumor(const float* mean, const float* U, int K, const double* w,
+                   const pcas_vol* vol, const double c_ref[3], int max_iter, double tol_mm,
+                   double c_out[3], void* stream);
+
+/* Eq. (3): per coefficient k, least-squares fit over t = L..T-1 of
+ * trace[t][k] ~ sum_{l=1..L} c[k][l-1] trace[t-l][k].  trace: host T x K;
+ * c: host K x L.  Needs T > 2L.  Host only. */
+int lp_fit(const double* trace, int T, int K, int L, double* c);
+
+/* Eq. (3): w0[k] = sum_l c[k][l-1] hist[l-1][k], hist[l-1] = w*(t-l) (host). */
+int lp_predict(const double* hist, const double* c, int K, int L, double* w0);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PCASOLVE_H */

@@ -161,17 +161,28 @@ static int sample_range(const ovol* vol, const oframe* F, const double dh[3], do
     return 1;
 }
 
-static int source_outside(const ovol* vol, const ocb* cb) {
+/* Every sample must lie ahead of the source (t > 0): require the whole
+ * support box [-1, n_c] to sit in the half-space in front of it, measured
+ * along the central ray direction ew (d . ew > 0 for every ray). */
+static int box_in_front(const ovol* vol, const ocb* cb) {
     oframe F;
     view_frame(cb, &F);
-    double q[3] = {(F.S[0] - vol->ox) / vol->sx, (F.S[1] - vol->oy) / vol->sy,
-                   (F.S[2] - vol->oz) / vol->sz};
-    return !in_support(vol, q);
+    double o[3] = {vol->ox, vol->oy, vol->oz}, s[3] = {vol->sx, vol->sy, vol->sz};
+    int n[3] = {vol->nx, vol->ny, vol->nz};
+    for (int corner = 0; corner < 8; corner++) {
+        double dot = 0;
+        for (int c = 0; c < 3; c++) {
+            double X = (corner >> c & 1) ? o[c] + n[c] * s[c] : o[c] - s[c];
+            dot += (X - F.S[c]) * F.ew[c];
+        }
+        if (!(dot > 0)) return 0;
+    }
+    return 1;
 }
 
 static int cb_ok(const ovol* vol, const ocb* cb, double step) {
     return cb && cb->nu > 0 && cb->nv > 0 && cb->sad > 0 && cb->sdd > 0 && cb->du > 0 &&
-           cb->dv > 0 && step > 0 && source_outside(vol, cb);
+           cb->dv > 0 && step > 0 && box_in_front(vol, cb);
 }
 
 /* --------------------------------------------------- projector P (Eq. 2) */

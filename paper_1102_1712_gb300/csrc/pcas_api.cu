@@ -1,0 +1,535 @@
+// pcas_api.cu -- the C ABI of libpcasolve (declared in include/pcasolve.h):
+// argument checks, view geometry in FP64 on the host, workspace layout, the
+// solve loop of the Appendix, and the small kernels (state set-up, tumour
+// localisation of Sec. II.A).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "pcas_internal.cuh"
+
+using namespace pcas;
+
+__device__ double d_localize_out[4];
+
+namespace {
+
+thread_local char g_err[512] = "";
+std::mutex g_localize_mutex;
+
+int fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define PCAS_CUDA(call)                                                                \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return fail(PCAS_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+int check_vol(const pcas_vol* v) {
+    if (!v) return fail(PCAS_ERR_INVALID_ARG, "vol is NULL");
+    if (v->nx < 1 || v->ny < 1 || v->nz < 1)
+        return fail(PCAS_ERR_INVALID_ARG, "volume dims must be positive (%d,%d,%d)", v->nx, v->ny, v->nz);
+    if ((double)v->nx * v->ny * v->nz > 2.0e9)
+        return fail(PCAS_ERR_INVALID_ARG, "volume has more than 2e9 voxels");
+    if (!(v->sx > 0) || !(v->sy > 0) || !(v->sz > 0))
+        return fail(PCAS_ERR_INVALID_ARG, "voxel spacing must be positive");
+    if (!isfinite(v->ox) || !isfinite(v->oy) || !isfinite(v->oz))
+        return fail(PCAS_ERR_INVALID_ARG, "volume origin must be finite");
+    return PCAS_OK;
+}
+
+Grid make_grid(const pcas_vol* v) {
+    Grid g;
+    g.nx = v->nx; g.ny = v->ny; g.nz = v->nz;
+    g.inv_sx = (float)(1.0 / v->sx); g.inv_sy = (float)(1.0 / v->sy); g.inv_sz = (float)(1.0 / v->sz);
+    return g;
+}
+
+// View geometry (header comment of pcasolve.h) in FP64, then rounded once.
+int make_view(const pcas_vol* vol, const pcas_cb* cb, double step, View* V) {
+    if (!cb) return fail(PCAS_ERR_INVALID_ARG, "cb is NULL");
+    if (cb->nu < 1 || cb->nv < 1 || (double)cb->nu * cb->nv > 1.0e9)
+        return fail(PCAS_ERR_INVALID_ARG, "detector size invalid (%d x %d)", cb->nu, cb->nv);
+    if (!(cb->sad > 0) || !(cb->sdd > 0) || !(cb->du > 0) || !(cb->dv > 0) || !isfinite(cb->angle_rad) ||
+        !isfinite(cb->off_u) || !isfinite(cb->off_v) || !isfinite(cb->sad) || !isfinite(cb->sdd))
+        return fail(PCAS_ERR_INVALID_ARG, "cone-beam geometry invalid");
+    if (!(step > 0) || !isfinite(step)) return fail(PCAS_ERR_INVALID_ARG, "step_mm must be > 0");
+    const double sa = sin(cb->angle_rad), ca = cos(cb->angle_rad);
+    const double S[3] = {cb->sad * sa, -cb->sad * ca, 0.0};
+    const double ew[3] = {-sa, ca, 0.0}, eu[3] = {ca, sa, 0.0}, ev[3] = {0.0, 0.0, 1.0};
+    const double o[3] = {vol->ox, vol->oy, vol->oz}, s[3] = {vol->sx, vol->sy, vol->sz};
+    const int n[3] = {vol->nx, vol->ny, vol->nz};
+    for (int corner = 0; corner < 8; corner++) {   // whole support box ahead of the source
+        double dot = 0;
+        for (int c = 0; c < 3; c++) {
+            double X = (corner >> c & 1) ? o[c] + n[c] * s[c] : o[c] - s[c];
+            dot += (X - S[c]) * ew[c];
+        }
+        if (!(dot > 0))
+            return fail(PCAS_ERR_INVALID_ARG, "the volume must lie entirely in front of the source");
+    }
+    if ((double)cb->sdd * 4.0 > 1e30) return fail(PCAS_ERR_INVALID_ARG, "sdd too large");
+    // sample indices i = t/step must stay far inside the int range
+    double far = cb->sad + 2.0 * (n[0] * s[0] + n[1] * s[1] + n[2] * s[2]);
+    if (far / step > 1.0e8) return fail(PCAS_ERR_INVALID_ARG, "step_mm too small for this geometry");
+    V->Q0 = make_float3((float)((S[0] - o[0]) / s[0]), (float)((S[1] - o[1]) / s[1]),
+                        (float)((S[2] - o[2]) / s[2]));
+    V->A = make_float3((float)(cb->sdd * ew[0] / s[0]), (float)(cb->sdd * ew[1] / s[1]),
+                       (float)(cb->sdd * ew[2] / s[2]));
+    V->Bu = make_float3((float)(eu[0] / s[0]), (float)(eu[1] / s[1]), (float)(eu[2] / s[2]));
+    V->Bv = make_float3((float)(ev[0] / s[0]), (float)(ev[1] / s[1]), (float)(ev[2] / s[2]));
+    V->EW = make_float3((float)(ew[0] * s[0]), (float)(ew[1] * s[1]), (float)(ew[2] * s[2]));
+    V->EU = make_float3((float)(eu[0] * s[0]), (float)(eu[1] * s[1]), (float)(eu[2] * s[2]));
+    V->EV = make_float3((float)(ev[0] * s[0]), (float)(ev[1] * s[1]), (float)(ev[2] * s[2]));
+    V->sdd = (float)cb->sdd;
+    V->sdd2 = (float)(cb->sdd * cb->sdd);
+    V->u0 = (float)(cb->off_u - 0.5 * (cb->nu - 1) * cb->du);
+    V->v0 = (float)(cb->off_v - 0.5 * (cb->nv - 1) * cb->dv);
+    V->du = (float)cb->du;
+    V->dv = (float)cb->dv;
+    V->nu = cb->nu;
+    V->nv = cb->nv;
+    V->step = (float)step;
+    return PCAS_OK;
+}
+
+int check_model(const float* mean, const float* U, int K) {
+    (void)mean;
+    if (K < 1 || K > PCAS_KMAX) return fail(PCAS_ERR_INVALID_ARG, "K must be in [1, %d], got %d", PCAS_KMAX, K);
+    if (!U) return fail(PCAS_ERR_INVALID_ARG, "U is NULL");
+    return PCAS_OK;
+}
+
+// ------------------------------------------------------------- workspace
+struct Layout {
+    size_t state, fpad, p0, p1, rayt, part_drr, part_res, part_adj, total;
+};
+
+Layout layout(const pcas_vol* vol, const pcas_cb* cb) {
+    Layout L;
+    Pad pd = make_pad(vol->nx, vol->ny, vol->nz);
+    size_t M = (size_t)cb->nu * cb->nv;
+    size_t off = 0;
+    L.state = off; off += align256(sizeof(SolveState));
+    L.fpad = off; off += align256((size_t)pd.px * pd.pny * pd.pnz * sizeof(float));
+    L.p0 = off; off += align256(M * sizeof(float));
+    L.p1 = off; off += align256(M * sizeof(float));
+    L.rayt = off; off += align256(M * sizeof(float4));
+    L.part_drr = off; off += align256((size_t)drr_blocks(cb->nu, cb->nv) * NMOM * sizeof(double));
+    L.part_res = off; off += align256((size_t)resid_blocks(cb->nu, cb->nv) * sizeof(double));
+    L.part_adj = off; off += align256((size_t)ADJ_MAX_BLOCKS * PCAS_KMAX * sizeof(double));
+    L.total = off;
+    return L;
+}
+
+struct Ws {
+    SolveState* st;
+    float *fpad, *p0, *p1;
+    float4* rayt;
+    double *part_drr, *part_res, *part_adj;
+};
+
+int bind_ws(void* ws, size_t ws_bytes, const pcas_vol* vol, const pcas_cb* cb, Ws* W) {
+    Layout L = layout(vol, cb);
+    if (!ws) return fail(PCAS_ERR_INVALID_ARG, "workspace is NULL");
+    if (((uintptr_t)ws & 255u) != 0) return fail(PCAS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (ws_bytes < L.total)
+        return fail(PCAS_ERR_INVALID_ARG, "workspace too small: %zu < %zu bytes", ws_bytes, L.total);
+    char* b = static_cast<char*>(ws);
+    W->st = reinterpret_cast<SolveState*>(b + L.state);
+    W->fpad = reinterpret_cast<float*>(b + L.fpad);
+    W->p0 = reinterpret_cast<float*>(b + L.p0);
+    W->p1 = reinterpret_cast<float*>(b + L.p1);
+    W->rayt = reinterpret_cast<float4*>(b + L.rayt);
+    W->part_drr = reinterpret_cast<double*>(b + L.part_drr);
+    W->part_res = reinterpret_cast<double*>(b + L.part_res);
+    W->part_adj = reinterpret_cast<double*>(b + L.part_adj);
+    return PCAS_OK;
+}
+
+int adjoint_block_cap() {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1024;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1024;
+    if (cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess) return 1024;
+    int cap = sms * (per_sm / 256);
+    return cap > 0 ? cap : 1024;
+}
+
+// ------------------------------------------------------------ small kernels
+__global__ void k_localize(const float* __restrict__ mean, const float* __restrict__ U, int K,
+                           Grid g, double w0, double w1, double w2, double w3, double w4, double w5,
+                           double w6, double w7, double ox, double oy, double oz, double isx,
+                           double isy, double isz, double cx, double cy, double cz, int max_iter,
+                           double tol, double* out) {
+    // one warp: lanes 0..7 own the eight taps of the trilinear DVF sample
+    const double w[PCAS_KMAX] = {w0, w1, w2, w3, w4, w5, w6, w7};
+    const int lane = threadIdx.x;
+    const long N = (long)g.nx * g.ny * g.nz;
+    double y[3] = {0.0, 0.0, 0.0};
+    int converged = 0, it = 0;
+    for (; it < max_iter; it++) {
+        double q[3] = {(cx + y[0] - ox) * isx, (cy + y[1] - oy) * isy, (cz + y[2] - oz) * isz};
+        double x[3] = {0.0, 0.0, 0.0};
+        if (lane < 8) {
+            bool inside = true;
+            double wt = 1.0;
+            long idx[3];
+            const int n[3] = {g.nx, g.ny, g.nz};
+            for (int c = 0; c < 3; c++) {
+                double qc = fmin(fmax(q[c], -2.0), (double)n[c] + 1.0);
+                double fl = floor(qc);
+                int bit = (lane >> c) & 1;
+                double z = qc - fl;
+                long l = (long)fl + bit;
+                wt *= bit ? z : 1.0 - z;
+                inside = inside && l >= 0 && l < n[c];
+                idx[c] = l;
+            }
+            if (inside && wt != 0.0) {
+                long v = (idx[2] * g.ny + idx[1]) * g.nx + idx[0];
+                for (int c = 0; c < 3; c++) {
+                    double val = mean ? (double)mean[c * N + v] : 0.0;
+                    for (int k = 0; k < K; k++) val += w[k] * (double)U[((long)k * 3 + c) * N + v];
+                    x[c] = wt * val;
+                }
+            }
+        }
+        double change = 0.0;
+        for (int c = 0; c < 3; c++) {
+            double s = warp_sum_d(x[c]);
+            double yn = -s;
+            change = fmax(change, fabs(yn - y[c]));
+            y[c] = yn;
+        }
+        if (change < tol) { converged = 1; break; }
+    }
+    if (lane == 0) {
+        out[0] = cx + y[0];
+        out[1] = cy + y[1];
+        out[2] = cz + y[2];
+        out[3] = converged ? 1.0 : 0.0;
+    }
+}
+
+// Reset the solver state for a new evaluation/solve.
+__global__ void k_init_state(SolveState* st, int K, double w0, double w1, double w2, double w3,
+                             double w4, double w5, double w6, double w7, double mu0, double alpha,
+                             double beta, double mu_min, int max_trials) {
+    if (threadIdx.x != 0) return;
+    const double w[PCAS_KMAX] = {w0, w1, w2, w3, w4, w5, w6, w7};
+    for (int k = 0; k < PCAS_KMAX; k++) {
+        st->w[k] = k < K ? w[k] : 0.0;
+        st->wt[k] = st->w[k];
+        st->d[k] = 0.0;
+        st->G[k] = 0.0;
+    }
+    st->gnorm = st->a = st->b = st->J = st->J0 = st->Jt = 0.0;
+    st->mu = mu0;
+    for (int i = 0; i < 2; i++)
+        for (int j = 0; j < NMOM; j++) st->mom[i][j] = 0.0;
+    st->mu0 = mu0; st->alpha = alpha; st->beta = beta; st->mu_min = mu_min;
+    st->K = K; st->max_trials = max_trials;
+    st->cur = 0; st->phase = PH_RUNNING; st->evals = 0; st->trials = 0;
+    for (int i = 0; i < 4; i++) st->counter[i] = 0u;
+}
+
+int launch_init(SolveState* st, int K, const double* w, const pcas_params* prm, cudaStream_t s) {
+    double v[PCAS_KMAX] = {0};
+    for (int k = 0; k < K; k++) v[k] = w[k];
+    pcas_params d = {0.2, 0.1, 0.5, 0.01, 10, 30, 1.0};
+    if (!prm) prm = &d;
+    k_init_state<<<1, 32, 0, s>>>(st, K, v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], prm->mu0,
+                                  prm->alpha, prm->beta, prm->mu_min, prm->max_trials);
+    PCAS_CUDA(cudaGetLastError());
+    return PCAS_OK;
+}
+
+int check_ptr(const void* p, const char* name) {
+    if (!p) return fail(PCAS_ERR_INVALID_ARG, "%s is NULL", name);
+    return PCAS_OK;
+}
+
+int check_finite(const double* v, int n, const char* name) {
+    for (int i = 0; i < n; i++)
+        if (!isfinite(v[i])) return fail(PCAS_ERR_INVALID_ARG, "%s[%d] is not finite", name, i);
+    return PCAS_OK;
+}
+
+#define PCAS_TRY(x)              \
+    do {                         \
+        int rc_ = (x);           \
+        if (rc_ != PCAS_OK) return rc_; \
+    } while (0)
+
+// Everything up to and including the gradient at st->w: warp, DRR with
+// moments, (A.1) + residual + J, fused adjoint gradient.
+int eval_gradient_pipeline(const float* f0, const float* mean, const float* U, int K, const float* y,
+                           const Grid& g, const Pad& pd, const View& V, const Ws& W, int step_setup,
+                           cudaStream_t s) {
+    WSrc ws{};
+    ws.dev = W.st->w;
+    ws.phase = &W.st->phase;
+    PCAS_CUDA(launch_warp_pca(f0, mean, U, K, ws, g, pd, W.fpad, s));
+    PCAS_CUDA(launch_drr_solver(W.fpad, g, pd, V, y, W.p0, W.p1, 0, W.st, W.part_drr, s));
+    PCAS_CUDA(launch_resid(W.p0, W.p1, y, V, 1, W.rayt, W.st, W.part_res, s));
+    PCAS_CUDA(launch_adjoint_grad(W.rayt, g, V, f0, mean, U, K, step_setup, W.st, W.part_adj,
+                                  adjoint_block_cap(), s));
+    return PCAS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pcas_last_error(void) { return g_err; }
+
+int pcas_version(void) { return PCAS_VERSION; }
+
+size_t pcas_workspace_bytes(const pcas_vol* vol, const pcas_cb* cb, int K) {
+    if (check_vol(vol) != PCAS_OK || !cb || cb->nu < 1 || cb->nv < 1 || K < 1 || K > PCAS_KMAX) return 0;
+    return layout(vol, cb).total;
+}
+
+int pca_dvf(const float* mean, const float* U, int K, const double* w, const pcas_vol* vol,
+            float* dvf, void* stream) {
+    PCAS_TRY(check_vol(vol));
+    PCAS_TRY(check_model(mean, U, K));
+    PCAS_TRY(check_ptr(w, "w"));
+    PCAS_TRY(check_ptr(dvf, "dvf"));
+    PCAS_TRY(check_finite(w, K, "w"));
+    float wf[PCAS_KMAX] = {0};
+    for (int k = 0; k < K; k++) wf[k] = (float)w[k];
+    PCAS_CUDA(launch_pca_dvf(mean, U, K, wf, make_grid(vol), dvf, as_stream(stream)));
+    return PCAS_OK;
+}
+
+int warp_volume(const float* f0, const float* dvf, const pcas_vol* vol, float* f, void* stream) {
+    PCAS_TRY(check_vol(vol));
+    PCAS_TRY(check_ptr(f0, "f0"));
+    PCAS_TRY(check_ptr(dvf, "dvf"));
+    PCAS_TRY(check_ptr(f, "f"));
+    PCAS_CUDA(launch_warp_dvf(f0, dvf, make_grid(vol), f, as_stream(stream)));
+    return PCAS_OK;
+}
+
+int drr_forward(const float* f, const pcas_vol* vol, const pcas_cb* cb, double step_mm, float* p,
+                void* stream) {
+    PCAS_TRY(check_vol(vol));
+    PCAS_TRY(check_ptr(f, "f"));
+    PCAS_TRY(check_ptr(p, "p"));
+    View V;
+    PCAS_TRY(make_view(vol, cb, step_mm, &V));
+    PCAS_CUDA(launch_drr_plain(f, make_grid(vol), V, p, as_stream(stream)));
+    return PCAS_OK;
+}
+
+int drr_adjoint(const float* img, const pcas_vol* vol, const pcas_cb* cb, double step_mm, float* g,
+                void* stream) {
+    PCAS_TRY(check_vol(vol));
+    PCAS_TRY(check_ptr(img, "img"));
+    PCAS_TRY(check_ptr(g, "g"));
+    View V;
+    PCAS_TRY(make_view(vol, cb, step_mm, &V));
+    PCAS_CUDA(launch_adjoint_plain(img, make_grid(vol), V, g, as_stream(stream)));
+    return PCAS_OK;
+}
+
+int cost_grad(const float* f0, const float* mean, const float* U, int K, const double* w,
+              const float* y, const pcas_vol* vol, const pcas_cb* cb, double step_mm, double* J,
+              double* dJdw, double* ab, void* ws, size_t ws_bytes, void* stream) {
+    PCAS_TRY(check_vol(vol));
+    PCAS_TRY(check_model(mean, U, K));
+    PCAS_TRY(check_ptr(f0, "f0"));
+    PCAS_TRY(check_ptr(y, "y"));
+    PCAS_TRY(check_ptr(w, "w"));
+    PCAS_TRY(check_ptr(J, "J"));
+    PCAS_TRY(check_ptr(dJdw, "dJdw"));
+    PCAS_TRY(check_ptr(ab, "ab"));
+    PCAS_TRY(check_finite(w, K, "w"));
+    View V;
+    PCAS_TRY(make_view(vol, cb, step_mm, &V));
+    Ws W;
+    PCAS_TRY(bind_ws(ws, ws_bytes, vol, cb, &W));
+    cudaStream_t s = as_stream(stream);
+    Grid g = make_grid(vol);
+    Pad pd = make_pad(vol->nx, vol->ny, vol->nz);
+    PCAS_CUDA(cudaMemsetAsync(W.fpad, 0, (size_t)pd.px * pd.pny * pd.pnz * sizeof(float), s));
+    PCAS_TRY(launch_init(W.st, K, w, nullptr, s));
+    PCAS_TRY(eval_gradient_pipeline(f0, mean, U, K, y, g, pd, V, W, 0, s));
+    SolveState h;
+    PCAS_CUDA(cudaMemcpyAsync(&h, W.st, sizeof(h), cudaMemcpyDeviceToHost, s));
+    PCAS_CUDA(cudaStreamSynchronize(s));
+    if (h.phase == PH_SINGULAR) return fail(PCAS_ERR_SINGULAR, "Y^T Y is singular (constant image y)");
+    *J = h.J;
+    for (int k = 0; k < K; k++) dJdw[k] = h.G[k];
+    ab[0] = h.a;
+    ab[1] = h.b;
+    return PCAS_OK;
+}
+
+int solve_projection(const float* f0, const float* mean, const float* U, int K, const float* y,
+                     const pcas_vol* vol, const pcas_cb* cb, const double* w_init,
+                     const pcas_params* prm, double* w_out, pcas_stats* stats, void* ws,
+                     size_t ws_bytes, void* stream) {
+    PCAS_TRY(check_vol(vol));
+    PCAS_TRY(check_model(mean, U, K));
+    PCAS_TRY(check_ptr(f0, "f0"));
+    PCAS_TRY(check_ptr(y, "y"));
+    PCAS_TRY(check_ptr(w_init, "w_init"));
+    PCAS_TRY(check_ptr(prm, "params"));
+    PCAS_TRY(check_ptr(w_out, "w_out"));
+    PCAS_TRY(check_finite(w_init, K, "w_init"));
+    if (!(prm->mu0 > 0) || !(prm->alpha >= 0) || !(prm->beta > 0 && prm->beta < 1) ||
+        !(prm->mu_min >= 0) || prm->max_iter < 0 || prm->max_trials < 0 || prm->max_trials > 1000)
+        return fail(PCAS_ERR_INVALID_ARG, "solver parameters out of range");
+    View V;
+    PCAS_TRY(make_view(vol, cb, prm->step_mm, &V));
+    Ws W;
+    PCAS_TRY(bind_ws(ws, ws_bytes, vol, cb, &W));
+    cudaStream_t s = as_stream(stream);
+    Grid g = make_grid(vol);
+    Pad pd = make_pad(vol->nx, vol->ny, vol->nz);
+    const int adj_cap = adjoint_block_cap();
+    PCAS_CUDA(cudaMemsetAsync(W.fpad, 0, (size_t)pd.px * pd.pny * pd.pnz * sizeof(float), s));
+    PCAS_TRY(launch_init(W.st, K, w_init, prm, s));
+    WSrc wcur{}, wtrial{};
+    wcur.dev = W.st->w;
+    wcur.phase = &W.st->phase;
+    wtrial.dev = W.st->wt;
+    wtrial.phase = &W.st->phase;
+    PCAS_CUDA(launch_warp_pca(f0, mean, U, K, wcur, g, pd, W.fpad, s));
+    PCAS_CUDA(launch_drr_solver(W.fpad, g, pd, V, y, W.p0, W.p1, 0, W.st, W.part_drr, s));
+    int iters = 0, phase = PH_RUNNING;
+    for (int it = 0; it < prm->max_iter; it++) {
+        PCAS_CUDA(launch_resid(W.p0, W.p1, y, V, it == 0, W.rayt, W.st, W.part_res, s));
+        PCAS_CUDA(launch_adjoint_grad(W.rayt, g, V, f0, mean, U, K, 1, W.st, W.part_adj, adj_cap, s));
+        // Armijo backtracking: each trial renders w + mu d and tests it on device;
+        // the host only reads the phase flag to decide whether to go on.
+        for (int tr = 0; tr <= prm->max_trials; tr++) {
+            PCAS_CUDA(launch_warp_pca(f0, mean, U, K, wtrial, g, pd, W.fpad, s));
+            PCAS_CUDA(launch_drr_solver(W.fpad, g, pd, V, y, W.p0, W.p1, 1, W.st, W.part_drr, s));
+            PCAS_CUDA(cudaMemcpyAsync(&phase, &W.st->phase, sizeof(int), cudaMemcpyDeviceToHost, s));
+            PCAS_CUDA(cudaStreamSynchronize(s));
+            if (phase != PH_RUNNING) break;
+        }
+        if (phase == PH_ACCEPT || phase == PH_STOP) iters++;
+        if (phase != PH_ACCEPT) break;
+    }
+    SolveState h;
+    PCAS_CUDA(cudaMemcpyAsync(&h, W.st, sizeof(h), cudaMemcpyDeviceToHost, s));
+    PCAS_CUDA(cudaStreamSynchronize(s));
+    if (h.phase == PH_SINGULAR) return fail(PCAS_ERR_SINGULAR, "Y^T Y is singular (constant image y)");
+    for (int k = 0; k < K; k++) w_out[k] = h.w[k];
+    if (stats) {
+        stats->iters = iters;
+        stats->evals = h.evals;
+        stats->status = PCAS_OK;
+        stats->J0 = h.J0;
+        stats->J = h.J;
+        stats->a = h.a;
+        stats->b = h.b;
+        stats->mu_last = h.mu;
+    }
+    return PCAS_OK;
+}
+
+int localize_tumor(const float* mean, const float* U, int K, const double* w, const pcas_vol* vol,
+                   const double c_ref[3], int max_iter, double tol_mm, double c_out[3],
+                   void* stream) {
+    PCAS_TRY(check_vol(vol));
+    PCAS_TRY(check_model(mean, U, K));
+    PCAS_TRY(check_ptr(w, "w"));
+    PCAS_TRY(check_ptr(c_ref, "c_ref"));
+    PCAS_TRY(check_ptr(c_out, "c_out"));
+    PCAS_TRY(check_finite(w, K, "w"));
+    PCAS_TRY(check_finite(c_ref, 3, "c_ref"));
+    if (max_iter < 1 || max_iter > 100000 || !(tol_mm > 0))
+        return fail(PCAS_ERR_INVALID_ARG, "max_iter must be in [1, 1e5] and tol_mm > 0");
+    double wv[PCAS_KMAX] = {0};
+    for (int k = 0; k < K; k++) wv[k] = w[k];
+    cudaStream_t s = as_stream(stream);
+    // The 32-byte result lands in a file-scope device slot and is copied out
+    // before the call returns; a host mutex keeps concurrent callers apart.
+    std::lock_guard<std::mutex> lock(g_localize_mutex);
+    double* out = nullptr;
+    PCAS_CUDA(cudaGetSymbolAddress((void**)&out, d_localize_out));
+    k_localize<<<1, 32, 0, s>>>(mean, U, K, make_grid(vol), wv[0], wv[1], wv[2], wv[3], wv[4], wv[5],
+                                wv[6], wv[7], vol->ox, vol->oy, vol->oz, 1.0 / vol->sx, 1.0 / vol->sy,
+                                1.0 / vol->sz, c_ref[0], c_ref[1], c_ref[2], max_iter, tol_mm, out);
+    PCAS_CUDA(cudaGetLastError());
+    double h[4];
+    PCAS_CUDA(cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, s));
+    PCAS_CUDA(cudaStreamSynchronize(s));
+    c_out[0] = h[0]; c_out[1] = h[1]; c_out[2] = h[2];
+    return h[3] != 0.0 ? PCAS_OK : PCAS_NOT_CONVERGED;
+}
+
+// Eq. (3) fit, host: per coefficient, normal equations of the order-L
+// least-squares predictor, Cholesky-free Gaussian elimination with pivoting.
+int lp_fit(const double* trace, int T, int K, int L, double* c) {
+    if (!trace || !c) return fail(PCAS_ERR_INVALID_ARG, "trace and c must be non-NULL");
+    if (K < 1 || L < 1 || L > 16 || T <= 2 * L)
+        return fail(PCAS_ERR_INVALID_ARG, "need K >= 1, 1 <= L <= 16 and T > 2L");
+    for (int k = 0; k < K; k++) {
+        double A[16][17];
+        memset(A, 0, sizeof(A));
+        for (int t = L; t < T; t++) {
+            double xt = trace[(long)t * K + k];
+            for (int a = 0; a < L; a++) {
+                double xa = trace[(long)(t - 1 - a) * K + k];
+                A[a][L] += xa * xt;
+                for (int b = 0; b < L; b++) A[a][b] += xa * trace[(long)(t - 1 - b) * K + k];
+            }
+        }
+        for (int col = 0; col < L; col++) {
+            int piv = col;
+            for (int r = col + 1; r < L; r++)
+                if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+            if (A[piv][col] == 0.0) return fail(PCAS_ERR_SINGULAR, "prediction normal equations singular");
+            if (piv != col)
+                for (int j = 0; j <= L; j++) {
+                    double t = A[col][j];
+                    A[col][j] = A[piv][j];
+                    A[piv][j] = t;
+                }
+            for (int r = col + 1; r < L; r++) {
+                double f = A[r][col] / A[col][col];
+                for (int j = col; j <= L; j++) A[r][j] -= f * A[col][j];
+            }
+        }
+        for (int r = L - 1; r >= 0; r--) {
+            double acc = A[r][L];
+            for (int j = r + 1; j < L; j++) acc -= A[r][j] * c[k * L + j];
+            c[k * L + r] = acc / A[r][r];
+        }
+    }
+    return PCAS_OK;
+}
+
+int lp_predict(const double* hist, const double* c, int K, int L, double* w0) {
+    if (!hist || !c || !w0) return fail(PCAS_ERR_INVALID_ARG, "hist, c and w0 must be non-NULL");
+    if (K < 1 || L < 1) return fail(PCAS_ERR_INVALID_ARG, "need K >= 1 and L >= 1");
+    for (int k = 0; k < K; k++) {
+        double acc = 0.0;
+        for (int l = 0; l < L; l++) acc += c[k * L + l] * hist[(long)l * K + k];
+        w0[k] = acc;
+    }
+    return PCAS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,279 @@
+// pcas_internal.cuh -- device-side types and helpers shared by the CUDA
+// translation units of libpcasolve (sm_103a).  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pcasolve.h"
+
+namespace pcas {
+
+// ----------------------------------------------------------------- geometry
+// One cone-beam view expressed in voxel units of the volume (q = (X - o) / s).
+// Ray of pixel (iu, iv): world direction d = sdd ew + u eu + v ev with
+// u = u0 + iu du, v = v0 + iv dv; since ew, eu, ev are orthonormal,
+// |d|^2 = sdd^2 + u^2 + v^2.  In voxel units D = (A + u Bu + v Bv) / |d|.
+struct View {
+    float3 Q0;               // source position (S - o) / s
+    float3 A, Bu, Bv;        // sdd ew / s, eu / s, ev / s
+    float3 EW, EU, EV;       // s * ew, s * eu, s * ev (voxel offsets -> mm along the axes)
+    float sdd, sdd2;
+    float u0, du, v0, dv;    // detector coordinates of pixel centres, mm
+    int nu, nv;
+    float step;              // ray-march step, mm
+};
+
+struct Grid {
+    int nx, ny, nz;
+    float inv_sx, inv_sy, inv_sz;
+};
+
+// Internal warped-volume layout with a zero halo: voxel (i,j,k) lives at
+// ((k+1) pny + (j+1)) px + (i+4).  px is a multiple of 4 and >= nx + 5, so the
+// interior rows start 16-byte aligned and every tap of a sample clamped to
+// [-1, n] stays inside the allocation.
+struct Pad {
+    int px, pny, pnz;
+};
+
+__host__ __device__ inline Pad make_pad(int nx, int ny, int nz) {
+    Pad p;
+    p.px = ((nx + 5) + 3) & ~3;
+    p.pny = ny + 2;
+    p.pnz = nz + 2;
+    return p;
+}
+
+// ----------------------------------------------------------- solver state
+enum Phase : int {
+    PH_RUNNING = 0,     // a trial is pending
+    PH_ACCEPT = 1,      // the last trial passed the Armijo test
+    PH_STOP = 2,        // no mu >= mu_min passed: iteration counted, solve ends
+    PH_ZERO_GRAD = 3,   // ||G|| = 0: solve ends before the line search
+    PH_SINGULAR = 4     // Y^T Y singular in Eq. (A.1)
+};
+
+enum { NMOM = 6 };      // Sp, Syp, Spp, Srr, Sy, Syy
+
+struct SolveState {
+    double w[PCAS_KMAX], wt[PCAS_KMAX], d[PCAS_KMAX], G[PCAS_KMAX];
+    double gnorm, a, b, J, J0, Jt, mu;
+    double mom[2][NMOM];            // final moments of the two projection buffers
+    double mu0, alpha, beta, mu_min;
+    int K, max_trials;
+    int cur;                        // buffer holding P f(w)
+    int phase, evals, trials;
+    unsigned int counter[4];        // last-block counters (reset by the last block)
+    int pad_[2];
+};
+
+// Reduction scratch: per-block partials plus the counter used to find the
+// last block to finish (which then reduces all partials in a fixed order).
+struct Reduce {
+    double* part;
+    unsigned int* counter;
+};
+
+// ------------------------------------------------------------- trilinear
+// Eq. (A.5): trilinear interpolation with zero outside the grid, on the dense
+// [nz][ny][nx] layout.  Positions are clamped to [-2, n+1] first so that
+// conversion to int is always defined (values there are zero anyway).
+__device__ __forceinline__ float tri_dense(const float* __restrict__ f, const Grid& g,
+                                           float qx, float qy, float qz) {
+    qx = fminf(fmaxf(qx, -2.0f), (float)g.nx + 1.0f);
+    qy = fminf(fmaxf(qy, -2.0f), (float)g.ny + 1.0f);
+    qz = fminf(fmaxf(qz, -2.0f), (float)g.nz + 1.0f);
+    float fx = floorf(qx), fy = floorf(qy), fz = floorf(qz);
+    int lx = (int)fx, ly = (int)fy, lz = (int)fz;
+    float zx = qx - fx, zy = qy - fy, zz = qz - fz;
+    const long sy = g.nx, sz = (long)g.nx * g.ny;
+    float v000, v100, v010, v110, v001, v101, v011, v111;
+    if (lx >= 0 && ly >= 0 && lz >= 0 && lx < g.nx - 1 && ly < g.ny - 1 && lz < g.nz - 1) {
+        const float* b = f + lz * sz + ly * sy + lx;
+        v000 = __ldg(b);          v100 = __ldg(b + 1);
+        v010 = __ldg(b + sy);     v110 = __ldg(b + sy + 1);
+        v001 = __ldg(b + sz);     v101 = __ldg(b + sz + 1);
+        v011 = __ldg(b + sz + sy); v111 = __ldg(b + sz + sy + 1);
+    } else {
+        const bool x0 = lx >= 0 && lx < g.nx, x1 = lx + 1 >= 0 && lx + 1 < g.nx;
+        const bool y0 = ly >= 0 && ly < g.ny, y1 = ly + 1 >= 0 && ly + 1 < g.ny;
+        const bool z0 = lz >= 0 && lz < g.nz, z1 = lz + 1 >= 0 && lz + 1 < g.nz;
+        auto at = [&](bool ok, int i, int j, int k) -> float {
+            return ok ? __ldg(f + k * sz + j * sy + i) : 0.0f;
+        };
+        v000 = at(x0 && y0 && z0, lx, ly, lz);
+        v100 = at(x1 && y0 && z0, lx + 1, ly, lz);
+        v010 = at(x0 && y1 && z0, lx, ly + 1, lz);
+        v110 = at(x1 && y1 && z0, lx + 1, ly + 1, lz);
+        v001 = at(x0 && y0 && z1, lx, ly, lz + 1);
+        v101 = at(x1 && y0 && z1, lx + 1, ly, lz + 1);
+        v011 = at(x0 && y1 && z1, lx, ly + 1, lz + 1);
+        v111 = at(x1 && y1 && z1, lx + 1, ly + 1, lz + 1);
+    }
+    float c00 = fmaf(zx, v100 - v000, v000), c10 = fmaf(zx, v110 - v010, v010);
+    float c01 = fmaf(zx, v101 - v001, v001), c11 = fmaf(zx, v111 - v011, v011);
+    float c0 = fmaf(zy, c10 - c00, c00), c1 = fmaf(zy, c11 - c01, c01);
+    return fmaf(zz, c1 - c0, c0);
+}
+
+// Same interpolant on the zero-halo layout: no bounds tests.  The floor is
+// clamped to [-1, n-1] and the fraction to [0, 1]; for q in [-1, n] this is
+// the same value (the clamped cases land on halo zeros with full weight).
+__device__ __forceinline__ float tri_padded(const float* __restrict__ f, const Grid& g,
+                                            const Pad& pd, float qx, float qy, float qz) {
+    float fx = fminf(fmaxf(floorf(qx), -1.0f), (float)(g.nx - 1));
+    float fy = fminf(fmaxf(floorf(qy), -1.0f), (float)(g.ny - 1));
+    float fz = fminf(fmaxf(floorf(qz), -1.0f), (float)(g.nz - 1));
+    float zx = __saturatef(qx - fx), zy = __saturatef(qy - fy), zz = __saturatef(qz - fz);
+    const int sy = pd.px, sz = pd.px * pd.pny;
+    const float* b = f + ((int)fz + 1) * sz + ((int)fy + 1) * sy + ((int)fx + 4);
+    float v000 = __ldg(b), v100 = __ldg(b + 1);
+    float v010 = __ldg(b + sy), v110 = __ldg(b + sy + 1);
+    float v001 = __ldg(b + sz), v101 = __ldg(b + sz + 1);
+    float v011 = __ldg(b + sz + sy), v111 = __ldg(b + sz + sy + 1);
+    float c00 = fmaf(zx, v100 - v000, v000), c10 = fmaf(zx, v110 - v010, v010);
+    float c01 = fmaf(zx, v101 - v001, v001), c11 = fmaf(zx, v111 - v011, v011);
+    float c0 = fmaf(zy, c10 - c00, c00), c1 = fmaf(zy, c11 - c01, c01);
+    return fmaf(zz, c1 - c0, c0);
+}
+
+// ----------------------------------------------------------------- rays
+// Unit ray direction of pixel (iu, iv) in voxel units per mm.
+__device__ __forceinline__ float3 ray_dir(const View& V, int iu, int iv) {
+    float u = fmaf((float)iu, V.du, V.u0), v = fmaf((float)iv, V.dv, V.v0);
+    float inv = 1.0f / sqrtf(V.sdd2 + u * u + v * v);
+    float3 D;
+    D.x = fmaf(u, V.Bu.x, fmaf(v, V.Bv.x, V.A.x)) * inv;
+    D.y = fmaf(u, V.Bu.y, fmaf(v, V.Bv.y, V.A.y)) * inv;
+    D.z = fmaf(u, V.Bu.z, fmaf(v, V.Bv.z, V.A.z)) * inv;
+    return D;
+}
+
+// Range [i0, i1] of sample indices whose position Q0 + i step D lies in the
+// support box [-1, n_c]; empty when i0 > i1.  Rounding can add or drop a
+// sample right on the box surface, where the interpolant is zero.
+__device__ __forceinline__ void sample_range(const View& V, const Grid& g, float3 D, int& i0,
+                                             int& i1) {
+    float tlo = -3.0e38f, thi = 3.0e38f;
+    const float q0[3] = {V.Q0.x, V.Q0.y, V.Q0.z};
+    const float d[3] = {D.x, D.y, D.z};
+    const float n[3] = {(float)g.nx, (float)g.ny, (float)g.nz};
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        if (d[c] != 0.0f) {
+            float ia = 1.0f / d[c];
+            float t1 = (-1.0f - q0[c]) * ia, t2 = (n[c] - q0[c]) * ia;
+            tlo = fmaxf(tlo, fminf(t1, t2));
+            thi = fminf(thi, fmaxf(t1, t2));
+        } else if (q0[c] < -1.0f || q0[c] > n[c]) {
+            tlo = 1.0f; thi = 0.0f;
+        }
+    }
+    if (tlo > thi) { i0 = 1; i1 = 0; return; }
+    i0 = (int)ceilf(tlo / V.step);
+    i1 = (int)floorf(thi / V.step);
+}
+
+// --------------------------------------------------------------- reductions
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-level reduction of NV per-thread float values: FP32 inside each warp,
+// FP64 across warps.  Writes this block's NV doubles to red.part[blk * NV + j]
+// and returns true in every thread of the block that finished last; that
+// block's thread j < NV then holds the fixed-order FP64 total in out[j]
+// (shared memory).  blockDim.x must be a multiple of 32, at most 1024.
+template <int NV>
+__device__ bool block_reduce_last(const float (&v)[NV], Reduce red, unsigned int nblocks,
+                                  unsigned int blk, double* out /* shared, NV */) {
+    __shared__ double s_w[32][NV];
+    __shared__ bool s_last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int j = 0; j < NV; j++) {
+        float t = warp_sum(v[j]);
+        if (lane == 0) s_w[wid][j] = (double)t;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double s = 0.0;
+        for (int w = 0; w < nw; w++) s += s_w[w][threadIdx.x];
+        red.part[(size_t)blk * NV + threadIdx.x] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int prev = atomicAdd(red.counter, 1u);
+        s_last = (prev == nblocks - 1);
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    // fixed-order reduction: thread t sums blocks t, t+nt, ...; then a tree
+    __shared__ double s_acc[1024 / 32][NV];
+    double acc[NV];
+#pragma unroll
+    for (int j = 0; j < NV; j++) acc[j] = 0.0;
+    for (unsigned int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+#pragma unroll
+        for (int j = 0; j < NV; j++) acc[j] += __ldcg(red.part + (size_t)b * NV + j);
+    }
+#pragma unroll
+    for (int j = 0; j < NV; j++) {
+        double t = warp_sum_d(acc[j]);
+        if (lane == 0) s_acc[wid][j] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double s = 0.0;
+        for (int w = 0; w < nw; w++) s += s_acc[w][threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+    if (threadIdx.x == 0) *red.counter = 0u;
+    __syncthreads();
+    return true;
+}
+
+// ------------------------------------------------------- launch interfaces
+struct WSrc {                 // where a PCA-model kernel takes w from
+    float w[PCAS_KMAX];       // used when dev is null
+    const double* dev;        // device w (solver state), K doubles
+    const int* phase;         // early exit when *phase >= PH_STOP (may be null)
+};
+
+cudaError_t launch_pca_dvf(const float* mean, const float* U, int K, const float* w, Grid g,
+                           float* dvf, cudaStream_t s);
+cudaError_t launch_warp_dvf(const float* f0, const float* dvf, Grid g, float* f, cudaStream_t s);
+cudaError_t launch_warp_pca(const float* f0, const float* mean, const float* U, int K, WSrc w,
+                            Grid g, Pad pd, float* fpad, cudaStream_t s);
+cudaError_t launch_drr_plain(const float* f, Grid g, const View& V, float* p, cudaStream_t s);
+cudaError_t launch_drr_solver(const float* fpad, Grid g, Pad pd, const View& V, const float* y,
+                              float* p0, float* p1, int trial, SolveState* st, double* part,
+                              cudaStream_t s);
+cudaError_t launch_resid(const float* p0, const float* p1, const float* y, const View& V,
+                         int first, float4* rayt, SolveState* st, double* part, cudaStream_t s);
+cudaError_t launch_adjoint_plain(const float* img, Grid g, const View& V, float* gout,
+                                 cudaStream_t s);
+cudaError_t launch_adjoint_grad(const float4* rayt, Grid g, const View& V, const float* f0,
+                                const float* mean, const float* U, int K, int step_setup,
+                                SolveState* st, double* part, int max_blocks, cudaStream_t s);
+cudaError_t launch_localize(const float* mean, const float* U, int K, const double* w, Grid g,
+                            const double o[3], const double s_mm[3], const double c_ref[3],
+                            int max_iter, double tol, double* out, cudaStream_t s);
+
+// Number of partial slots each solver kernel needs (sizes the workspace).
+inline unsigned drr_blocks(int nu, int nv) { return (unsigned)((nu + 7) / 8) * ((nv + 15) / 16); }
+inline unsigned resid_blocks(int nu, int nv) { return (unsigned)(((long)nu * nv + 255) / 256); }
+enum { ADJ_MAX_BLOCKS = 4096 };
+
+}  // namespace pcas

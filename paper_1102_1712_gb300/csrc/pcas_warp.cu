@@ -1,0 +1,154 @@
+// pcas_warp.cu -- DVF synthesis (Eq. 1) fused into the trilinear warp of the
+// reference CT (Eq. A.3/A.5).  HBM-bound: the motion model (12 (K+1) bytes per
+// voxel) streams once per evaluation with 16-byte loads and evict-first
+// policy, f0 is gathered through L1/L2, and f is written once.
+#include "pcas_internal.cuh"
+
+namespace pcas {
+namespace {
+
+constexpr int kWarpThreads = 256;
+
+__device__ __forceinline__ float4 ld4_stream(const float* p) {
+    return __ldcs(reinterpret_cast<const float4*>(p));
+}
+
+// Eq. (1) on four consecutive voxels: x_c = mean_c + sum_k w_k U_kc.
+__device__ __forceinline__ void dvf4(const float* __restrict__ mean, const float* __restrict__ U,
+                                     int K, const float* w, long N, long n, float x[3][4]) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        float4 m = mean ? ld4_stream(mean + c * N + n) : make_float4(0.f, 0.f, 0.f, 0.f);
+        x[c][0] = m.x; x[c][1] = m.y; x[c][2] = m.z; x[c][3] = m.w;
+    }
+    for (int k = 0; k < K; k++) {
+        const float wk = w[k];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            float4 u = ld4_stream(U + ((long)k * 3 + c) * N + n);
+            x[c][0] = fmaf(wk, u.x, x[c][0]);
+            x[c][1] = fmaf(wk, u.y, x[c][1]);
+            x[c][2] = fmaf(wk, u.z, x[c][2]);
+            x[c][3] = fmaf(wk, u.w, x[c][3]);
+        }
+    }
+}
+
+// Eq. (1) alone: dvf = mean + U w.  One thread per 4 voxels (VEC) or 1 voxel.
+template <bool VEC>
+__global__ void __launch_bounds__(kWarpThreads)
+k_pca_dvf(const float* __restrict__ mean, const float* __restrict__ U, int K, WSrc ws, long N,
+          float* __restrict__ dvf) {
+    long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (VEC) {
+        long n = t * 4;
+        if (n >= N) return;
+        float x[3][4];
+        dvf4(mean, U, K, ws.w, N, n, x);
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+            *reinterpret_cast<float4*>(dvf + c * N + n) = make_float4(x[c][0], x[c][1], x[c][2], x[c][3]);
+    } else {
+        if (t >= N) return;
+        for (int c = 0; c < 3; c++) {
+            float x = mean ? mean[c * N + t] : 0.0f;
+            for (int k = 0; k < K; k++) x = fmaf(ws.w[k], U[((long)k * 3 + c) * N + t], x);
+            dvf[c * N + t] = x;
+        }
+    }
+}
+
+// Warp by an explicit DVF (public warp_volume): one voxel per thread, dense out.
+__global__ void __launch_bounds__(kWarpThreads)
+k_warp_dvf(const float* __restrict__ f0, const float* __restrict__ dvf, Grid g, long N,
+           float* __restrict__ f) {
+    long n = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    int i = (int)(n % g.nx);
+    long r = n / g.nx;
+    int j = (int)(r % g.ny), k = (int)(r / g.ny);
+    float qx = fmaf(dvf[n], g.inv_sx, (float)i);
+    float qy = fmaf(dvf[N + n], g.inv_sy, (float)j);
+    float qz = fmaf(dvf[2 * N + n], g.inv_sz, (float)k);
+    f[n] = tri_dense(f0, g, qx, qy, qz);
+}
+
+// Fused DVF synthesis + warp into the zero-halo layout used by the solver.
+// VEC: 4 voxels per thread along x (nx % 4 == 0, 16-byte aligned model).
+template <bool VEC>
+__global__ void __launch_bounds__(kWarpThreads)
+k_warp_pca(const float* __restrict__ f0, const float* __restrict__ mean,
+           const float* __restrict__ U, int K, WSrc ws, Grid g, Pad pd, long N,
+           float* __restrict__ fpad) {
+    if (ws.phase && *ws.phase >= PH_STOP) return;
+    __shared__ float s_w[PCAS_KMAX];
+    if (threadIdx.x < PCAS_KMAX)
+        s_w[threadIdx.x] = ws.dev ? (threadIdx.x < K ? (float)ws.dev[threadIdx.x] : 0.f)
+                                  : ws.w[threadIdx.x];
+    __syncthreads();
+    long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (VEC) {
+        long n = t * 4;
+        if (n >= N) return;
+        int i = (int)(n % g.nx);
+        long r = n / g.nx;
+        int j = (int)(r % g.ny), k = (int)(r / g.ny);
+        float x[3][4];
+        dvf4(mean, U, K, s_w, N, n, x);
+        float o[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++)
+            o[e] = tri_dense(f0, g, fmaf(x[0][e], g.inv_sx, (float)(i + e)),
+                             fmaf(x[1][e], g.inv_sy, (float)j), fmaf(x[2][e], g.inv_sz, (float)k));
+        float* dst = fpad + ((long)(k + 1) * pd.pny + (j + 1)) * pd.px + (i + 4);
+        *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+    } else {
+        if (t >= N) return;
+        int i = (int)(t % g.nx);
+        long r = t / g.nx;
+        int j = (int)(r % g.ny), k = (int)(r / g.ny);
+        float x[3];
+        for (int c = 0; c < 3; c++) {
+            float v = mean ? mean[c * N + t] : 0.0f;
+            for (int kk = 0; kk < K; kk++) v = fmaf(s_w[kk], U[((long)kk * 3 + c) * N + t], v);
+            x[c] = v;
+        }
+        fpad[((long)(k + 1) * pd.pny + (j + 1)) * pd.px + (i + 4)] =
+            tri_dense(f0, g, fmaf(x[0], g.inv_sx, (float)i), fmaf(x[1], g.inv_sy, (float)j),
+                      fmaf(x[2], g.inv_sz, (float)k));
+    }
+}
+
+inline bool aligned16(const void* p) { return p == nullptr || ((uintptr_t)p & 15u) == 0; }
+
+inline unsigned blocks_for(long work) { return (unsigned)((work + kWarpThreads - 1) / kWarpThreads); }
+
+}  // namespace
+
+cudaError_t launch_pca_dvf(const float* mean, const float* U, int K, const float* w, Grid g,
+                           float* dvf, cudaStream_t s) {
+    long N = (long)g.nx * g.ny * g.nz;
+    WSrc ws{};
+    for (int k = 0; k < K && k < PCAS_KMAX; k++) ws.w[k] = w[k];
+    bool vec = (N % 4 == 0) && aligned16(mean) && aligned16(U) && aligned16(dvf);
+    if (vec) k_pca_dvf<true><<<blocks_for(N / 4), kWarpThreads, 0, s>>>(mean, U, K, ws, N, dvf);
+    else k_pca_dvf<false><<<blocks_for(N), kWarpThreads, 0, s>>>(mean, U, K, ws, N, dvf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_warp_dvf(const float* f0, const float* dvf, Grid g, float* f, cudaStream_t s) {
+    long N = (long)g.nx * g.ny * g.nz;
+    k_warp_dvf<<<blocks_for(N), kWarpThreads, 0, s>>>(f0, dvf, g, N, f);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_warp_pca(const float* f0, const float* mean, const float* U, int K, WSrc w,
+                            Grid g, Pad pd, float* fpad, cudaStream_t s) {
+    long N = (long)g.nx * g.ny * g.nz;
+    bool vec = (g.nx % 4 == 0) && aligned16(mean) && aligned16(U) && aligned16(fpad);
+    if (vec) k_warp_pca<true><<<blocks_for(N / 4), kWarpThreads, 0, s>>>(f0, mean, U, K, w, g, pd, N, fpad);
+    else k_warp_pca<false><<<blocks_for(N), kWarpThreads, 0, s>>>(f0, mean, U, K, w, g, pd, N, fpad);
+    return cudaGetLastError();
+}
+
+}  // namespace pcas

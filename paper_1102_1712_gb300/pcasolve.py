@@ -1,0 +1,300 @@
+"""Thin ctypes binding of libpcasolve (include/pcasolve.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Device arrays are torch CUDA tensors (float32, contiguous); the
+current torch stream is passed to the library.  There is no CPU fallback: if
+the library is missing, loading raises.
+
+Names follow the C ABI: pca_dvf, warp_volume, drr_forward, drr_adjoint,
+cost_grad, solve_projection, localize_tumor, lp_fit, lp_predict.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpcasolve.so")
+KMAX = 8
+
+OK, INVALID_ARG, SINGULAR, CUDA_ERROR, NOT_CONVERGED, TIMEOUT = range(6)
+
+
+class PcasError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"pcasolve error {code}: {msg}")
+        self.code = code
+
+
+class Vol(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("sx", C.c_double), ("sy", C.c_double), ("sz", C.c_double),
+                ("ox", C.c_double), ("oy", C.c_double), ("oz", C.c_double)]
+
+
+class CB(C.Structure):
+    _fields_ = [("sad", C.c_double), ("sdd", C.c_double), ("nu", C.c_int), ("nv", C.c_int),
+                ("du", C.c_double), ("dv", C.c_double), ("off_u", C.c_double),
+                ("off_v", C.c_double), ("angle_rad", C.c_double)]
+
+
+class Params(C.Structure):
+    _fields_ = [("mu0", C.c_double), ("alpha", C.c_double), ("beta", C.c_double),
+                ("mu_min", C.c_double), ("max_iter", C.c_int), ("max_trials", C.c_int),
+                ("step_mm", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("evals", C.c_int), ("status", C.c_int),
+                ("J0", C.c_double), ("J", C.c_double), ("a", C.c_double),
+                ("b", C.c_double), ("mu_last", C.c_double)]
+
+
+_D = C.POINTER(C.c_double)
+_P = C.c_void_p
+_lock = threading.Lock()
+_lib = None
+
+_SIGS = {
+    "pcas_last_error": (C.c_char_p, []),
+    "pcas_version": (C.c_int, []),
+    "pcas_workspace_bytes": (C.c_size_t, [C.POINTER(Vol), C.POINTER(CB), C.c_int]),
+    "pca_dvf": (C.c_int, [_P, _P, C.c_int, _D, C.POINTER(Vol), _P, _P]),
+    "warp_volume": (C.c_int, [_P, _P, C.POINTER(Vol), _P, _P]),
+    "drr_forward": (C.c_int, [_P, C.POINTER(Vol), C.POINTER(CB), C.c_double, _P, _P]),
+    "drr_adjoint": (C.c_int, [_P, C.POINTER(Vol), C.POINTER(CB), C.c_double, _P, _P]),
+    "cost_grad": (C.c_int, [_P, _P, _P, C.c_int, _D, _P, C.POINTER(Vol), C.POINTER(CB), C.c_double,
+                            _D, _D, _D, _P, C.c_size_t, _P]),
+    "solve_projection": (C.c_int, [_P, _P, _P, C.c_int, _P, C.POINTER(Vol), C.POINTER(CB), _D,
+                                   C.POINTER(Params), _D, C.POINTER(Stats), _P, C.c_size_t, _P]),
+    "localize_tumor": (C.c_int, [_P, _P, C.c_int, _D, C.POINTER(Vol), _D, C.c_int, C.c_double, _D, _P]),
+    "lp_fit": (C.c_int, [_D, C.c_int, C.c_int, C.c_int, _D]),
+    "lp_predict": (C.c_int, [_D, _D, C.c_int, C.c_int, _D]),
+}
+
+
+def lib():
+    """Load libpcasolve.so (built in-tree by ``paper_1102_1712_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"{LIB_PATH} is missing: build it with paper_1102_1712_gb300.build.build() "
+                    "(or __graft_entry__.build()); there is no fallback path")
+            L = C.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().pcas_last_error().decode(errors="replace")
+
+
+def _check(rc, allow=(OK,)):
+    if rc not in allow:
+        raise PcasError(rc, last_error())
+    return rc
+
+
+# ------------------------------------------------------------ marshalling
+def vol_struct(v) -> Vol:
+    if isinstance(v, Vol):
+        return v
+    return Vol(v["nx"], v["ny"], v["nz"], v["sx"], v["sy"], v["sz"], v["ox"], v["oy"], v["oz"])
+
+
+def cb_struct(g) -> CB:
+    if isinstance(g, CB):
+        return g
+    return CB(g["sad"], g["sdd"], g["nu"], g["nv"], g["du"], g["dv"], g.get("off_u", 0.0),
+              g.get("off_v", 0.0), g["angle"])
+
+
+def params_struct(p) -> Params:
+    if isinstance(p, Params):
+        return p
+    return Params(p["mu0"], p["alpha"], p["beta"], p["mu_min"], int(p["max_iter"]),
+                  int(p["max_trials"]), p["step"])
+
+
+def _dev(t, name, numel=None):
+    """Device pointer of a contiguous float32 CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError(f"{name} must be contiguous float32")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return t.data_ptr()
+
+
+def _stream(stream=None):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+
+
+def _host_d(a, n=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def _nvox(vol):
+    v = vol_struct(vol)
+    return v.nx * v.ny * v.nz
+
+
+def _K(U, vol):
+    N = _nvox(vol)
+    if U.numel() % (3 * N):
+        raise ValueError("U must hold K x 3 x N values")
+    return U.numel() // (3 * N)
+
+
+# ------------------------------------------------------------------- API
+def workspace_bytes(vol, cb, K) -> int:
+    return int(lib().pcas_workspace_bytes(C.byref(vol_struct(vol)), C.byref(cb_struct(cb)), int(K)))
+
+
+class Workspace:
+    """A 256-byte aligned device workspace for cost_grad / solve_projection."""
+
+    def __init__(self, vol, cb, K, device=None):
+        import torch
+        n = workspace_bytes(vol, cb, K)
+        if n == 0:
+            raise ValueError("invalid volume / view / K for a workspace")
+        self.buf = torch.empty(n + 256, dtype=torch.uint8, device=device or "cuda")
+        base = self.buf.data_ptr()
+        self.ptr = (base + 255) & ~255
+        self.nbytes = n
+
+
+def pca_dvf(mean, U, w, vol, out=None, stream=None):
+    import torch
+    N = _nvox(vol)
+    K = _K(U, vol)
+    wv = _host_d(w, K)
+    if out is None:
+        out = torch.empty(3 * N, dtype=torch.float32, device=U.device)
+    _check(lib().pca_dvf(_dev(mean, "mean", 3 * N), _dev(U, "U"), K, wv.ctypes.data_as(_D),
+                         C.byref(vol_struct(vol)), _dev(out, "dvf", 3 * N), _stream(stream)))
+    return out
+
+
+def warp_volume(f0, dvf, vol, out=None, stream=None):
+    import torch
+    N = _nvox(vol)
+    if out is None:
+        out = torch.empty(N, dtype=torch.float32, device=f0.device)
+    _check(lib().warp_volume(_dev(f0, "f0", N), _dev(dvf, "dvf", 3 * N), C.byref(vol_struct(vol)),
+                             _dev(out, "f", N), _stream(stream)))
+    return out
+
+
+def drr_forward(f, vol, cb, step, out=None, stream=None):
+    import torch
+    g = cb_struct(cb)
+    if out is None:
+        out = torch.empty(g.nu * g.nv, dtype=torch.float32, device=f.device)
+    _check(lib().drr_forward(_dev(f, "f", _nvox(vol)), C.byref(vol_struct(vol)), C.byref(g),
+                             float(step), _dev(out, "p", g.nu * g.nv), _stream(stream)))
+    return out
+
+
+def drr_adjoint(img, vol, cb, step, out=None, stream=None):
+    import torch
+    g = cb_struct(cb)
+    N = _nvox(vol)
+    if out is None:
+        out = torch.empty(N, dtype=torch.float32, device=img.device)
+    _check(lib().drr_adjoint(_dev(img, "img", g.nu * g.nv), C.byref(vol_struct(vol)), C.byref(g),
+                             float(step), _dev(out, "g", N), _stream(stream)))
+    return out
+
+
+def cost_grad(f0, mean, U, w, y, vol, cb, step, ws: Workspace = None, stream=None):
+    """Returns (J, dJ/dw (K,), (a, b)) at w."""
+    N = _nvox(vol)
+    K = _K(U, vol)
+    g = cb_struct(cb)
+    ws = ws or Workspace(vol, cb, K, device=U.device)
+    wv = _host_d(w, K)
+    J = C.c_double()
+    G = np.zeros(K)
+    ab = np.zeros(2)
+    _check(lib().cost_grad(_dev(f0, "f0", N), _dev(mean, "mean", 3 * N), _dev(U, "U"), K,
+                           wv.ctypes.data_as(_D), _dev(y, "y", g.nu * g.nv), C.byref(vol_struct(vol)),
+                           C.byref(g), float(step), C.byref(J), G.ctypes.data_as(_D),
+                           ab.ctypes.data_as(_D), ws.ptr, ws.nbytes, _stream(stream)))
+    return J.value, G, (ab[0], ab[1])
+
+
+def solve_projection(f0, mean, U, y, vol, cb, w_init, params, ws: Workspace = None, stream=None):
+    """Returns (w (K,), stats dict)."""
+    N = _nvox(vol)
+    K = _K(U, vol)
+    g = cb_struct(cb)
+    ws = ws or Workspace(vol, cb, K, device=U.device)
+    w0 = _host_d(w_init, K)
+    w_out = np.zeros(K)
+    st = Stats()
+    prm = params_struct(params)
+    _check(lib().solve_projection(_dev(f0, "f0", N), _dev(mean, "mean", 3 * N), _dev(U, "U"), K,
+                                  _dev(y, "y", g.nu * g.nv), C.byref(vol_struct(vol)), C.byref(g),
+                                  w0.ctypes.data_as(_D), C.byref(prm), w_out.ctypes.data_as(_D),
+                                  C.byref(st), ws.ptr, ws.nbytes, _stream(stream)))
+    return w_out, {k: getattr(st, k) for k, _ in Stats._fields_}
+
+
+def localize_tumor(mean, U, w, vol, c_ref, max_iter=50, tol_mm=1e-6, stream=None):
+    """Returns (c (3,), converged)."""
+    N = _nvox(vol)
+    K = _K(U, vol)
+    wv = _host_d(w, K)
+    cr = _host_d(c_ref, 3)
+    out = np.zeros(3)
+    rc = lib().localize_tumor(_dev(mean, "mean", 3 * N), _dev(U, "U"), K, wv.ctypes.data_as(_D),
+                              C.byref(vol_struct(vol)), cr.ctypes.data_as(_D), int(max_iter),
+                              float(tol_mm), out.ctypes.data_as(_D), _stream(stream))
+    _check(rc, allow=(OK, NOT_CONVERGED))
+    return out, rc == OK
+
+
+def lp_fit(trace, L):
+    tr = np.ascontiguousarray(trace, dtype=np.float64)
+    T, K = tr.shape
+    c = np.zeros((K, L))
+    _check(lib().lp_fit(tr.ctypes.data_as(_D), T, K, int(L), c.ctypes.data_as(_D)))
+    return c
+
+
+def lp_predict(hist, c):
+    """hist[l-1] = w*(t-l), shape (L, K); c shape (K, L)."""
+    h = np.ascontiguousarray(hist, dtype=np.float64)
+    cc = np.ascontiguousarray(c, dtype=np.float64)
+    L, K = h.shape
+    w0 = np.zeros(K)
+    _check(lib().lp_predict(h.ctypes.data_as(_D), cc.ctypes.data_as(_D), K, L, w0.ctypes.data_as(_D)))
+    return w0
+
+
+def default_params(step_mm, **kw):
+    """Appendix constants scaled for O(1) coefficients (mu0 2 -> 0.2, mu_min 0.1 -> 0.01)."""
+    d = dict(mu0=0.2, alpha=0.1, beta=0.5, mu_min=0.01, max_iter=10, max_trials=30, step=float(step_mm))
+    d.update(kw)
+    return d

@@ -1,0 +1,138 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds and loads,
+exports every function include/pcasolve.h declares, rejects invalid arguments
+before touching the device, and its host-only routines (Eq. 3) agree with the
+oracle."""
+import ctypes as C
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1102_1712_gb300 import build as B
+from paper_1102_1712_gb300 import pcasolve as P
+from paper_1102_1712_gb300 import synth as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return P.lib()
+
+
+def declared_functions():
+    names = []
+    inc = os.path.join(ROOT, "include")
+    for fn in sorted(os.listdir(inc)):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(inc, fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([A-Za-z_]\w*)\s*\([^;{]*\)\s*;", text, re.M):
+            names.append(m.group(1))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    for must in ["pca_dvf", "warp_volume", "drr_forward", "drr_adjoint", "cost_grad",
+                 "solve_projection", "localize_tumor", "lp_fit", "lp_predict",
+                 "pcas_workspace_bytes", "pcas_last_error", "pcas_version"]:
+        assert must in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert lib.pcas_version() == 1
+
+
+def test_binding_exposes_the_same_names():
+    for n in ["pca_dvf", "warp_volume", "drr_forward", "drr_adjoint", "cost_grad",
+              "solve_projection", "localize_tumor", "lp_fit", "lp_predict"]:
+        assert callable(getattr(P, n))
+
+
+def test_workspace_bytes_host_only(lib):
+    vol = S.volume(256, 256, 100, 2.0, 2.0, 2.5)
+    cb = S.cone_beam(512, 384, 0.776, 0.776)
+    n = P.workspace_bytes(vol, cb, 3)
+    pad = (((256 + 5) + 3) // 4 * 4) * 258 * 102 * 4
+    assert n >= pad + 512 * 384 * (4 + 4 + 16) and n % 256 == 0
+    assert n < pad + 512 * 384 * 24 + 2_000_000
+    assert P.workspace_bytes(vol, cb, 0) == 0 and P.workspace_bytes(vol, cb, 9) == 0
+
+
+FAKE = C.c_void_p(0x1000)    # never dereferenced: every call below fails its host checks
+
+
+def _vol(**kw):
+    v = dict(S.volume(16, 16, 8, 2.0, 2.0, 2.0)); v.update(kw); return P.vol_struct(v)
+
+
+def _cb(**kw):
+    g = dict(S.cone_beam(32, 24, 1.5, 1.5, 0.3)); g.update(kw); return P.cb_struct(g)
+
+
+@pytest.mark.parametrize("vol,cb,step", [
+    (_vol(nx=0), _cb(), 1.0),
+    (_vol(sx=-1.0), _cb(), 1.0),
+    (_vol(), _cb(nu=0), 1.0),
+    (_vol(), _cb(du=0.0), 1.0),
+    (_vol(), _cb(), 0.0),
+    (_vol(), _cb(), float("nan")),
+    (_vol(), _cb(sad=10.0, sdd=20.0), 1.0),            # volume not in front of the source
+    (_vol(ox=float("inf")), _cb(), 1.0),
+])
+def test_invalid_geometry_rejected_before_launch(lib, vol, cb, step):
+    rc = lib.drr_forward(FAKE, C.byref(vol), C.byref(cb), step, FAKE, None)
+    assert rc == P.INVALID_ARG and P.last_error()
+    rc = lib.drr_adjoint(FAKE, C.byref(vol), C.byref(cb), step, FAKE, None)
+    assert rc == P.INVALID_ARG
+
+
+def test_invalid_model_and_workspace_rejected(lib):
+    vol, cb = _vol(), _cb()
+    w = np.zeros(8)
+    D = C.POINTER(C.c_double)
+    J = C.c_double()
+    G = np.zeros(8)
+    ab = np.zeros(2)
+    assert lib.pca_dvf(None, FAKE, 0, w.ctypes.data_as(D), C.byref(vol), FAKE, None) == P.INVALID_ARG
+    assert lib.pca_dvf(None, FAKE, 9, w.ctypes.data_as(D), C.byref(vol), FAKE, None) == P.INVALID_ARG
+    assert lib.pca_dvf(None, None, 3, w.ctypes.data_as(D), C.byref(vol), FAKE, None) == P.INVALID_ARG
+    bad = w.copy(); bad[1] = np.nan
+    assert lib.pca_dvf(None, FAKE, 3, bad.ctypes.data_as(D), C.byref(vol), FAKE, None) == P.INVALID_ARG
+    need = lib.pcas_workspace_bytes(C.byref(vol), C.byref(cb), 3)
+    args = (FAKE, None, FAKE, 3, w.ctypes.data_as(D), FAKE, C.byref(vol), C.byref(cb), 1.0,
+            C.byref(J), G.ctypes.data_as(D), ab.ctypes.data_as(D))
+    assert lib.cost_grad(*args, C.c_void_p(0x100000), need - 1, None) == P.INVALID_ARG
+    assert "too small" in P.last_error()
+    assert lib.cost_grad(*args, C.c_void_p(0x100010), need, None) == P.INVALID_ARG
+    assert "aligned" in P.last_error()
+    assert lib.cost_grad(*args, None, need, None) == P.INVALID_ARG
+    prm = P.params_struct(P.default_params(1.0, beta=1.5))
+    st = P.Stats()
+    wo = np.zeros(3)
+    assert lib.solve_projection(FAKE, None, FAKE, 3, FAKE, C.byref(vol), C.byref(cb), w.ctypes.data_as(D),
+                                C.byref(prm), wo.ctypes.data_as(D), C.byref(st), C.c_void_p(0x100000),
+                                need, None) == P.INVALID_ARG
+    c = np.zeros(3)
+    assert lib.localize_tumor(None, FAKE, 3, w.ctypes.data_as(D), C.byref(vol), c.ctypes.data_as(D), 0,
+                              1e-6, c.ctypes.data_as(D), None) == P.INVALID_ARG
+
+
+def test_lp_fit_and_predict_match_oracle(lib):
+    W = S.breathing_trace(300, 10.0, irregular=True, seed=5)
+    for L in (1, 2, 3):
+        np.testing.assert_allclose(P.lp_fit(W, L), O.lp_fit(W, L), rtol=1e-10, atol=1e-12)
+    c = O.lp_fit(W, 2)
+    hist = W[[9, 8]]
+    np.testing.assert_allclose(P.lp_predict(hist, c), O.lp_predict(hist, c), rtol=1e-14, atol=1e-15)
+    with pytest.raises(P.PcasError):
+        P.lp_fit(W[:4], 2)
+    t = np.arange(100) / 10.0
+    c = P.lp_fit(np.sin(2 * math.pi * t / 4.0)[:, None], 2)
+    assert abs(c[0, 0] - 2 * math.cos(2 * math.pi / 40)) < 1e-9 and abs(c[0, 1] + 1) < 1e-9
