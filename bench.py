@@ -1,0 +1,405 @@
+"""Benchmark: projections/s of the single-projection PCA motion solve on the
+paper-shaped sequence workload (256x256x100 CT at 2x2x2.5 mm, K = 3, 512x384
+detector at 0.776 mm, 600 views over 360 deg at 10 fps, sinusoidal 4 s / 15 mm
+breathing), one step = one projection: linear-prediction warm start (Eq. 3),
+the alternating solve of the Appendix (warp + DRR + adjoint iterations with
+Armijo backtracking) and tumour localisation (Sec. II.A).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on the host cores over a bounded sample of the same workload.
+Inputs are synthetic (seeded phantom, eigenvector fields and breathing trace);
+the measured projections are rendered on the GPU by this library's own warp
+and projector at the planted coefficients plus 1 % Gaussian noise.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="sequence-256x256x100-K3-512x384", vol=(256, 256, 100, 2.0, 2.0, 2.5), K=3,
+                det=(512, 384, 0.776, 0.776), n_proj=600, fps=10.0, period_s=4.0, amp_mm=15.0,
+                tumor_mm=20.0, seeds=dict(phantom=10, dvf=11, noise=12), noise=0.01)
+METRIC = "projections/s solved (warp+DRR+adjoint iters), % HBM roofline, mm error"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=120)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--irregular", action="store_true", help="irregular breathing trace")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------- inputs
+def make_inputs(irregular: bool):
+    from paper_1102_1712_gb300 import synth as S
+    W = WORKLOAD
+    vol = S.volume(*W["vol"])
+    f0, c_ref = S.phantom(vol, W["tumor_mm"], seed=W["seeds"]["phantom"])
+    U = S.eigen_dvfs(vol, W["K"], seed=W["seeds"]["dvf"])
+    if irregular:
+        trace = S.breathing_trace(W["n_proj"], W["fps"], W["period_s"], W["amp_mm"], K=W["K"],
+                                  irregular=True, drift_mm=3.0, seed=13)
+    else:
+        trace = S.breathing_trace(W["n_proj"], W["fps"], W["period_s"], W["amp_mm"], K=W["K"])
+    # prediction model fitted on the regular training trace at the projection rate (Sec. II.A)
+    train = S.breathing_trace(400, W["fps"], W["period_s"], W["amp_mm"], K=W["K"], t0=0.37)
+    angles = S.gantry_angles(W["n_proj"], 360.0)
+    return vol, f0, c_ref, U, trace, train, angles
+
+
+def view(angle):
+    from paper_1102_1712_gb300 import synth as S
+    d = WORKLOAD["det"]
+    return S.cone_beam(d[0], d[1], d[2], d[3], float(angle))
+
+
+def step_mm():
+    v = WORKLOAD["vol"]
+    return 0.5 * min(v[3], v[4], v[5])
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------- algorithmic bytes
+def kernel_bytes(N, M, K, has_mean):
+    """Algorithmic HBM bytes per launch of each solver kernel (float32)."""
+    model = 12 * K * N + (12 * N if has_mean else 0)
+    return {
+        "warp_pca": model + 4 * N + 4 * N,           # model read, f0 read once, f written
+        "drr_solver": 4 * N + 4 * M + 4 * M,         # f read once, y read, p written
+        "resid": 4 * M + 4 * M + 16 * M,             # p, y read; ray table written
+        "adjoint_grad": model + 4 * N + 16 * M,      # model + f0 re-read; ray table read
+    }
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+# ------------------------------------------------------------- our arm
+def run_ours(args, ws_, rank, local):
+    import torch
+
+    from paper_1102_1712_gb300 import build as B
+    from paper_1102_1712_gb300 import pcasolve as P
+    from paper_1102_1712_gb300 import synth as S
+
+    if rank == 0 or not B.up_to_date():
+        B.build()
+    if ws_ > 1:
+        torch.distributed.barrier()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    vol, f0, c_ref, U, trace, train, angles = make_inputs(args.irregular)
+    K, N = WORKLOAD["K"], f0.size
+    d = WORKLOAD["det"]
+    M = d[0] * d[1]
+    step = step_mm()
+    tf0 = torch.from_numpy(f0.ravel()).to(dev)
+    tU = torch.from_numpy(U.ravel()).to(dev)
+    W_, K_ = args.warmup, args.steps
+    n_used = W_ + K_
+    if n_used > WORKLOAD["n_proj"]:
+        raise SystemExit(f"warmup + steps must be <= {WORKLOAD['n_proj']}")
+    # measured projections: P f(w_true(t)) rendered by the library + seeded noise
+    ys = torch.empty((n_used, M), dtype=torch.float32, device=dev)
+    c_true = np.zeros((n_used, 3))
+    for t in range(n_used):
+        f = P.warp_volume(tf0, P.pca_dvf(None, tU, trace[t], vol), vol)
+        p = P.drr_forward(f, vol, view(angles[t]), step)
+        sigma = WORKLOAD["noise"] * float(p.abs().max())
+        ys[t] = p + torch.from_numpy(S.gaussian_noise(M, sigma, seed=1000 * WORKLOAD["seeds"]["noise"] + t)).to(dev)
+        c_true[t], _ = P.localize_tumor(None, tU, trace[t], vol, c_ref)
+    c_lp = P.lp_fit(train, 2)
+    prm = P.default_params(step)
+    wsp = P.Workspace(vol, view(0.0), K, device=dev)
+    torch.cuda.synchronize()
+
+    def solve_range(t0, t1, hist, y_of, stats_out):
+        for t in range(t0, t1):
+            if t == 0:
+                w0 = np.zeros(K)
+            elif t == 1:
+                w0 = hist[-1]
+            else:
+                w0 = P.lp_predict(np.stack([hist[-1], hist[-2]]), c_lp)
+            w, st = P.solve_projection(tf0, None, tU, y_of(t), vol, view(angles[t]), w0, prm, ws=wsp)
+            c, _ = P.localize_tumor(None, tU, w, vol, c_ref)
+            hist.append(w)
+            stats_out.append((t, st, c))
+
+    # warm-up projections (also builds the prediction history)
+    hist, warm = [], []
+    solve_range(0, W_, hist, lambda t: ys[t], warm)
+    torch.cuda.synchronize()
+
+    # ---- timed region: inputs resident in HBM
+    stream = torch.cuda.current_stream()
+    P.profile(True)
+    timed = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        if ws_ > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        solve_range(W_, n_used, hist, lambda t: ys[t], timed)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if ws_ > 1:
+            torch.distributed.barrier()
+    ms = ev0.elapsed_time(ev1)
+    prof = P.profile_read()
+    P.profile(False)
+    clocks = clk.summary()
+
+    # ---- end to end: per step, y from pinned host memory, result back to host
+    y_host = ys.cpu().pin_memory()
+    y_dev = torch.empty(M, dtype=torch.float32, device=dev)
+    hist_e2e = list(hist[:W_])
+    e2e_stats = []
+
+    def y_e2e(t):
+        y_dev.copy_(y_host[t], non_blocking=True)
+        return y_dev
+
+    if ws_ > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solve_range(W_, n_used, hist_e2e, y_e2e, e2e_stats)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1)
+    if ws_ > 1:
+        torch.distributed.barrier()
+
+    # ---- aggregate over ranks (max time)
+    t_s, te_s = ms / 1e3, ms_e2e / 1e3
+    if ws_ > 1:
+        tt = torch.tensor([t_s, te_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_s, te_s = float(tt[0]), float(tt[1])
+    if rank != 0:
+        return None
+
+    errs = np.array([np.linalg.norm(c - c_true[t]) for t, _, c in timed])
+    iters = np.array([st["iters"] for _, st, _ in timed])
+    evals = np.array([st["evals"] for _, st, _ in timed])
+    pk, pk_kind = peaks()
+    kb = kernel_bytes(N, M, K, False)
+    kernels = {}
+    for name in ("warp_pca", "drr_solver", "resid", "adjoint_grad"):
+        n, tot = prof[name]
+        if n:
+            avg = tot / n
+            gbs = kb[name] / (avg * 1e-3) / 1e9
+            kernels[name] = {"launches": n, "total_ms": round(tot, 3), "avg_ms": round(avg, 4),
+                             "share": round(tot / ms, 4), "alg_bytes": kb[name],
+                             "achieved_gbs": round(gbs, 1), "frac_hbm": round(gbs / pk["hbm_gbs"], 4)}
+    dom = max(kernels, key=lambda k: kernels[k]["total_ms"])
+    launches = sum(n for n, _ in prof.values())
+    total_alg = sum(kernels[k]["alg_bytes"] * kernels[k]["launches"] for k in kernels)
+    line = {
+        "metric": METRIC,
+        "value": round(ws_ * K_ / t_s, 3),
+        "unit": "projections/s",
+        "n_gpus": ws_,
+        "steps": K_,
+        "warmup": W_,
+        "ms_per_step": round(1e3 * t_s / K_, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded ellipsoid phantom, smoothed random eigen-DVFs, sinusoidal trace; "
+                "projections rendered by this library + 1% noise)",
+        "config": {"workload": WORKLOAD["name"] + ("-irregular" if args.irregular else "-regular"),
+                   "volume": "256x256x100 @ 2x2x2.5 mm", "K": K, "detector": "512x384 @ 0.776 mm",
+                   "step_mm": step, "projections": f"{W_}+{K_} of 600 over 360 deg",
+                   "solver": "mu0=0.2 alpha=0.1 beta=0.5 mu_min=0.01 max_iter=10",
+                   "l2": "inputs larger than L2 (motion model 236 MB streamed per evaluation)",
+                   "parallelism": "replicas" if ws_ > 1 else "single"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["achieved_gbs"],
+                     "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": kernels[dom]["frac_hbm"],
+                     "traffic": None, "peak_source": pk_kind,
+                     "path_alg_gbs": round(total_alg / t_s / 1e9, 1),
+                     "path_frac": round(total_alg / t_s / 1e9 / pk["hbm_gbs"], 4)},
+        "kernels": kernels,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "mm_error": {"mean": round(float(errs.mean()), 4), "p95": round(float(np.percentile(errs, 95)), 4),
+                     "max": round(float(errs.max()), 4)},
+        "solver": {"iters_mean": round(float(iters.mean()), 3), "evals_mean": round(float(evals.mean()), 3)},
+        "e2e": {"value": round(ws_ * K_ / te_s, 3), "unit": "projections/s",
+                "h2d_bytes_per_step": 4 * M,
+                # solver state read back at the end (488 B), one 4-byte flag per trial, 32 B of centroid
+                "d2h_bytes_per_step": int(round(488 + 4 * (float(evals.mean()) - 1) + 32))},
+    }
+    if ws_ == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(vol, f0, c_ref, U, trace, train, angles, ys, W_)
+    return line
+
+
+# ------------------------------------------------------- oracle timings
+def oracle_solve_one(O, vol, f0, U, y, angle, w0, step):
+    from paper_1102_1712_gb300 import synth as S  # noqa: F401  (inputs only)
+    prm = dict(mu0=0.2, alpha=0.1, beta=0.5, mu_min=0.01, max_iter=10, max_trials=30, step=step)
+    return O.solve_projection(f0, None, U, y, vol, view(angle), w0, prm)
+
+
+def cpu_baseline(vol, f0, c_ref, U, trace, train, angles, ys, t):
+    """The oracle (FP64 C, OpenMP over rays) solving one projection of the
+    workload, warm-started from the prediction of the planted coefficients."""
+    import oracle as O
+    c_lp = O.lp_fit(train, 2)
+    w0 = O.lp_predict(np.stack([trace[t - 1], trace[t - 2]]), c_lp)
+    y = ys[t].cpu().numpy()
+    t0 = time.perf_counter()
+    w, st, _ = oracle_solve_one(O, vol, f0, U, y, angles[t], w0, step_mm())
+    O.localize_tumor(None, U, w, vol, c_ref)
+    dt = time.perf_counter() - t0
+    return {"value": round(1.0 / dt, 5), "unit": "projections/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"1 projection (#{t}) of the same workload, full solve ({st['iters']} iterations, "
+                      f"{st['evals']} evaluations) + localisation, {dt:.1f} s"}
+
+
+def run_reference(args, ws_, rank):
+    """Oracle arm: solves projections of the workload on the host cores, each
+    warm-started from the prediction of the planted coefficients, until
+    ``steps`` projections or a 150 s budget are done (bounded sample)."""
+    if rank != 0:
+        return None
+    import oracle as O
+    from paper_1102_1712_gb300 import synth as S
+    O.build()
+    vol, f0, c_ref, U, trace, train, angles = make_inputs(args.irregular)
+    step = step_mm()
+    c_lp = O.lp_fit(train, 2)
+    d = WORKLOAD["det"]
+    done, t_total, budget = 0, 0.0, 150.0
+    for i in range(args.warmup + args.steps):
+        t = 2 + i
+        cb = view(angles[t])
+        p = O.drr_forward(O.warp_volume(f0, O.pca_dvf(None, U, trace[t], vol), vol), vol, cb, step)
+        y = (p + S.gaussian_noise(p.size, WORKLOAD["noise"] * np.abs(p).max(),
+                                  seed=1000 * WORKLOAD["seeds"]["noise"] + t, dtype=np.float64)).astype(np.float32)
+        w0 = O.lp_predict(np.stack([trace[t - 1], trace[t - 2]]), c_lp)
+        t0 = time.perf_counter()
+        w, st, _ = oracle_solve_one(O, vol, f0, U, y, angles[t], w0, step)
+        O.localize_tumor(None, U, w, vol, c_ref)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup or args.warmup + args.steps == 1:
+            done += 1
+            t_total += dt
+        if t_total > budget or (i < args.warmup and dt > budget / 4):
+            break
+    done = max(done, 1)
+    t_total = max(t_total, 1e-9)
+    value = done / t_total
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "projections/s",
+            "n_gpus": 1, "steps": done, "warmup": args.warmup, "ms_per_step": round(1e3 * t_total / done, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic, same workload as our arm", "config": {"workload": WORKLOAD["name"]},
+            "cpu_baseline": {"value": round(value, 5), "unit": "projections/s", "cores": os.cpu_count(),
+                             "kind": "oracle",
+                             "sample": f"{done} projections of the workload, full solves, 150 s budget"},
+            "e2e": {"value": round(value, 5), "unit": "projections/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    ws_, rank, local = dist_env()
+    if ws_ > 1 and args.impl == "ours":
+        import torch
+        torch.distributed.init_process_group("nccl")
+    if args.impl == "reference":
+        line = run_reference(args, ws_, rank)
+    else:
+        line = run_ours(args, ws_, rank, local)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if ws_ > 1 and args.impl == "ours":
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

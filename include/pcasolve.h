@@ -147,6 +147,31 @@ int lp_fit(const double* trace, int T, int K, int L, double* c);
 /* Eq. (3): w0[k] = sum_l c[k][l-1] hist[l-1][k], hist[l-1] = w*(t-l) (host). */
 int lp_predict(const double* hist, const double* c, int K, int L, double* w0);
 
+/* ------------------------------------------------------------------------
+ * Benchmark instrumentation (the paper has no counterpart).  The library
+ * counts every kernel it launches, per kernel class.  pcas_profile(1) resets
+ * the counts and, until pcas_profile(0), also brackets each launch with a
+ * pair of CUDA events recorded on the launch stream (events come from a pool
+ * created on the first pcas_profile(1); up to 65536 launches are timed).
+ * pcas_profile_read() returns the launches and the summed event time in ms
+ * of one class since the last reset; it waits for the recorded events.
+ * These calls are host-side and thread-safe. */
+enum {
+    PCAS_K_WARP_PCA = 0,     /* fused Eq. (1) + (A.5) into the solver volume   */
+    PCAS_K_DRR_SOLVER = 1,   /* solver P with fused moments / Armijo test      */
+    PCAS_K_RESID = 2,        /* Eq. (A.1) + residual + J                        */
+    PCAS_K_ADJ_GRAD = 3,     /* fused P^T, Eq. (A.8) and dJ/dw reduction        */
+    PCAS_K_DRR = 4,          /* drr_forward                                     */
+    PCAS_K_ADJ = 5,          /* drr_adjoint                                     */
+    PCAS_K_PCA_DVF = 6,      /* pca_dvf                                         */
+    PCAS_K_WARP_DVF = 7,     /* warp_volume                                     */
+    PCAS_K_LOCALIZE = 8,     /* localize_tumor                                  */
+    PCAS_K_INIT = 9,         /* solver state reset                              */
+    PCAS_K_COUNT = 10
+};
+int pcas_profile(int on);
+int pcas_profile_read(int kind, long long* launches, double* total_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,6 +35,42 @@ int fail(int code, const char* fmt, ...) {
             return fail(PCAS_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
+
+// ------------------------------------------------------------- profiling
+// Launch counts per kernel class (always) and, while enabled, CUDA-event
+// brackets around each launch, recorded on the launch stream.
+constexpr int kProfSlots = 65536;
+std::mutex g_prof_mutex;
+long long g_launches[PCAS_K_COUNT];
+bool g_prof_on = false;
+cudaEvent_t* g_ev = nullptr;           // 2 * kProfSlots events, created once
+int g_ev_kind[kProfSlots];
+int g_ev_used = 0;
+
+int prof_begin(int kind, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g_prof_mutex);
+    g_launches[kind]++;
+    if (!g_prof_on || !g_ev || g_ev_used >= kProfSlots) return -1;
+    int slot = g_ev_used++;
+    g_ev_kind[slot] = kind;
+    cudaEventRecord(g_ev[2 * slot], s);
+    return slot;
+}
+
+void prof_end(int slot, cudaStream_t s) {
+    if (slot < 0) return;
+    cudaEventRecord(g_ev[2 * slot + 1], s);
+}
+
+#define PCAS_LAUNCH(kind, s, expr)                                                          \
+    do {                                                                                    \
+        int slot_ = prof_begin((kind), (s));                                                \
+        cudaError_t e_ = (expr);                                                            \
+        prof_end(slot_, (s));                                                               \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(PCAS_ERR_CUDA, "%s failed: %s", #expr, cudaGetErrorString(e_));     \
+    } while (0)
+
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -253,9 +289,11 @@ int launch_init(SolveState* st, int K, const double* w, const pcas_params* prm, 
     for (int k = 0; k < K; k++) v[k] = w[k];
     pcas_params d = {0.2, 0.1, 0.5, 0.01, 10, 30, 1.0};
     if (!prm) prm = &d;
-    k_init_state<<<1, 32, 0, s>>>(st, K, v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], prm->mu0,
-                                  prm->alpha, prm->beta, prm->mu_min, prm->max_trials);
-    PCAS_CUDA(cudaGetLastError());
+    PCAS_LAUNCH(PCAS_K_INIT, s,
+                (k_init_state<<<1, 32, 0, s>>>(st, K, v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7],
+                                               prm->mu0, prm->alpha, prm->beta, prm->mu_min,
+                                               prm->max_trials),
+                 cudaGetLastError()));
     return PCAS_OK;
 }
 
@@ -284,17 +322,56 @@ int eval_gradient_pipeline(const float* f0, const float* mean, const float* U, i
     WSrc ws{};
     ws.dev = W.st->w;
     ws.phase = &W.st->phase;
-    PCAS_CUDA(launch_warp_pca(f0, mean, U, K, ws, g, pd, W.fpad, s));
-    PCAS_CUDA(launch_drr_solver(W.fpad, g, pd, V, y, W.p0, W.p1, 0, W.st, W.part_drr, s));
-    PCAS_CUDA(launch_resid(W.p0, W.p1, y, V, 1, W.rayt, W.st, W.part_res, s));
-    PCAS_CUDA(launch_adjoint_grad(W.rayt, g, V, f0, mean, U, K, step_setup, W.st, W.part_adj,
-                                  adjoint_block_cap(), s));
+    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, K, ws, g, pd, W.fpad, s));
+    PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
+                launch_drr_solver(W.fpad, g, pd, V, y, W.p0, W.p1, 0, W.st, W.part_drr, s));
+    PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.p0, W.p1, y, V, 1, W.rayt, W.st, W.part_res, s));
+    PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
+                launch_adjoint_grad(W.rayt, g, V, f0, mean, U, K, step_setup, W.st, W.part_adj,
+                                    adjoint_block_cap(), s));
     return PCAS_OK;
 }
 
 }  // namespace
 
 extern "C" {
+
+int pcas_profile(int on) {
+    std::lock_guard<std::mutex> lk(g_prof_mutex);
+    for (int k = 0; k < PCAS_K_COUNT; k++) g_launches[k] = 0;
+    g_ev_used = 0;
+    if (on && !g_ev) {
+        cudaEvent_t* ev = new cudaEvent_t[2 * kProfSlots];
+        for (int i = 0; i < 2 * kProfSlots; i++) {
+            cudaError_t e = cudaEventCreate(&ev[i]);
+            if (e != cudaSuccess) {
+                for (int j = 0; j < i; j++) cudaEventDestroy(ev[j]);
+                delete[] ev;
+                return fail(PCAS_ERR_CUDA, "cudaEventCreate failed: %s", cudaGetErrorString(e));
+            }
+        }
+        g_ev = ev;
+    }
+    g_prof_on = on != 0;
+    return PCAS_OK;
+}
+
+int pcas_profile_read(int kind, long long* launches, double* total_ms) {
+    if (kind < 0 || kind >= PCAS_K_COUNT || !launches || !total_ms)
+        return fail(PCAS_ERR_INVALID_ARG, "bad profile query");
+    std::lock_guard<std::mutex> lk(g_prof_mutex);
+    *launches = g_launches[kind];
+    double ms = 0.0;
+    for (int i = 0; i < g_ev_used; i++) {
+        if (g_ev_kind[i] != kind) continue;
+        float t = 0.f;
+        PCAS_CUDA(cudaEventSynchronize(g_ev[2 * i + 1]));
+        PCAS_CUDA(cudaEventElapsedTime(&t, g_ev[2 * i], g_ev[2 * i + 1]));
+        ms += t;
+    }
+    *total_ms = ms;
+    return PCAS_OK;
+}
 
 const char* pcas_last_error(void) { return g_err; }
 
@@ -314,7 +391,8 @@ int pca_dvf(const float* mean, const float* U, int K, const double* w, const pca
     PCAS_TRY(check_finite(w, K, "w"));
     float wf[PCAS_KMAX] = {0};
     for (int k = 0; k < K; k++) wf[k] = (float)w[k];
-    PCAS_CUDA(launch_pca_dvf(mean, U, K, wf, make_grid(vol), dvf, as_stream(stream)));
+    cudaStream_t s = as_stream(stream);
+    PCAS_LAUNCH(PCAS_K_PCA_DVF, s, launch_pca_dvf(mean, U, K, wf, make_grid(vol), dvf, s));
     return PCAS_OK;
 }
 
@@ -323,7 +401,8 @@ int warp_volume(const float* f0, const float* dvf, const pcas_vol* vol, float* f
     PCAS_TRY(check_ptr(f0, "f0"));
     PCAS_TRY(check_ptr(dvf, "dvf"));
     PCAS_TRY(check_ptr(f, "f"));
-    PCAS_CUDA(launch_warp_dvf(f0, dvf, make_grid(vol), f, as_stream(stream)));
+    cudaStream_t s = as_stream(stream);
+    PCAS_LAUNCH(PCAS_K_WARP_DVF, s, launch_warp_dvf(f0, dvf, make_grid(vol), f, s));
     return PCAS_OK;
 }
 
@@ -334,7 +413,8 @@ int drr_forward(const float* f, const pcas_vol* vol, const pcas_cb* cb, double s
     PCAS_TRY(check_ptr(p, "p"));
     View V;
     PCAS_TRY(make_view(vol, cb, step_mm, &V));
-    PCAS_CUDA(launch_drr_plain(f, make_grid(vol), V, p, as_stream(stream)));
+    cudaStream_t s = as_stream(stream);
+    PCAS_LAUNCH(PCAS_K_DRR, s, launch_drr_plain(f, make_grid(vol), V, p, s));
     return PCAS_OK;
 }
 
@@ -345,7 +425,8 @@ int drr_adjoint(const float* img, const pcas_vol* vol, const pcas_cb* cb, double
     PCAS_TRY(check_ptr(g, "g"));
     View V;
     PCAS_TRY(make_view(vol, cb, step_mm, &V));
-    PCAS_CUDA(launch_adjoint_plain(img, make_grid(vol), V, g, as_stream(stream)));
+    cudaStream_t s = as_stream(stream);
+    PCAS_LAUNCH(PCAS_K_ADJ, s, launch_adjoint_plain(img, make_grid(vol), V, g, s));
     return PCAS_OK;
 }
 
@@ -412,17 +493,20 @@ int solve_projection(const float* f0, const float* mean, const float* U, int K, 
     wcur.phase = &W.st->phase;
     wtrial.dev = W.st->wt;
     wtrial.phase = &W.st->phase;
-    PCAS_CUDA(launch_warp_pca(f0, mean, U, K, wcur, g, pd, W.fpad, s));
-    PCAS_CUDA(launch_drr_solver(W.fpad, g, pd, V, y, W.p0, W.p1, 0, W.st, W.part_drr, s));
+    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, K, wcur, g, pd, W.fpad, s));
+    PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
+                launch_drr_solver(W.fpad, g, pd, V, y, W.p0, W.p1, 0, W.st, W.part_drr, s));
     int iters = 0, phase = PH_RUNNING;
     for (int it = 0; it < prm->max_iter; it++) {
-        PCAS_CUDA(launch_resid(W.p0, W.p1, y, V, it == 0, W.rayt, W.st, W.part_res, s));
-        PCAS_CUDA(launch_adjoint_grad(W.rayt, g, V, f0, mean, U, K, 1, W.st, W.part_adj, adj_cap, s));
+        PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.p0, W.p1, y, V, it == 0, W.rayt, W.st, W.part_res, s));
+        PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
+                    launch_adjoint_grad(W.rayt, g, V, f0, mean, U, K, 1, W.st, W.part_adj, adj_cap, s));
         // Armijo backtracking: each trial renders w + mu d and tests it on device;
         // the host only reads the phase flag to decide whether to go on.
         for (int tr = 0; tr <= prm->max_trials; tr++) {
-            PCAS_CUDA(launch_warp_pca(f0, mean, U, K, wtrial, g, pd, W.fpad, s));
-            PCAS_CUDA(launch_drr_solver(W.fpad, g, pd, V, y, W.p0, W.p1, 1, W.st, W.part_drr, s));
+            PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, K, wtrial, g, pd, W.fpad, s));
+            PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
+                        launch_drr_solver(W.fpad, g, pd, V, y, W.p0, W.p1, 1, W.st, W.part_drr, s));
             PCAS_CUDA(cudaMemcpyAsync(&phase, &W.st->phase, sizeof(int), cudaMemcpyDeviceToHost, s));
             PCAS_CUDA(cudaStreamSynchronize(s));
             if (phase != PH_RUNNING) break;
@@ -468,10 +552,12 @@ int localize_tumor(const float* mean, const float* U, int K, const double* w, co
     std::lock_guard<std::mutex> lock(g_localize_mutex);
     double* out = nullptr;
     PCAS_CUDA(cudaGetSymbolAddress((void**)&out, d_localize_out));
-    k_localize<<<1, 32, 0, s>>>(mean, U, K, make_grid(vol), wv[0], wv[1], wv[2], wv[3], wv[4], wv[5],
-                                wv[6], wv[7], vol->ox, vol->oy, vol->oz, 1.0 / vol->sx, 1.0 / vol->sy,
-                                1.0 / vol->sz, c_ref[0], c_ref[1], c_ref[2], max_iter, tol_mm, out);
-    PCAS_CUDA(cudaGetLastError());
+    PCAS_LAUNCH(PCAS_K_LOCALIZE, s,
+                (k_localize<<<1, 32, 0, s>>>(mean, U, K, make_grid(vol), wv[0], wv[1], wv[2], wv[3],
+                                             wv[4], wv[5], wv[6], wv[7], vol->ox, vol->oy, vol->oz,
+                                             1.0 / vol->sx, 1.0 / vol->sy, 1.0 / vol->sz, c_ref[0],
+                                             c_ref[1], c_ref[2], max_iter, tol_mm, out),
+                 cudaGetLastError()));
     double h[4];
     PCAS_CUDA(cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, s));
     PCAS_CUDA(cudaStreamSynchronize(s));

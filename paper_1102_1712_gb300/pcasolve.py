@@ -73,7 +73,13 @@ _SIGS = {
     "localize_tumor": (C.c_int, [_P, _P, C.c_int, _D, C.POINTER(Vol), _D, C.c_int, C.c_double, _D, _P]),
     "lp_fit": (C.c_int, [_D, C.c_int, C.c_int, C.c_int, _D]),
     "lp_predict": (C.c_int, [_D, _D, C.c_int, C.c_int, _D]),
+    "pcas_profile": (C.c_int, [C.c_int]),
+    "pcas_profile_read": (C.c_int, [C.c_int, C.POINTER(C.c_longlong), _D]),
 }
+
+# kernel classes of pcas_profile_read (include/pcasolve.h)
+KERNELS = ["warp_pca", "drr_solver", "resid", "adjoint_grad", "drr_forward", "drr_adjoint",
+           "pca_dvf", "warp_volume", "localize", "init"]
 
 
 def lib():
@@ -291,6 +297,22 @@ def lp_predict(hist, c):
     w0 = np.zeros(K)
     _check(lib().lp_predict(h.ctypes.data_as(_D), cc.ctypes.data_as(_D), K, L, w0.ctypes.data_as(_D)))
     return w0
+
+
+def profile(on: bool):
+    """Reset the per-kernel launch counters; time every launch with CUDA events while on."""
+    _check(lib().pcas_profile(1 if on else 0))
+
+
+def profile_read():
+    """{kernel class: (launches, summed event ms)} since the last profile() reset."""
+    out = {}
+    for i, name in enumerate(KERNELS):
+        n = C.c_longlong()
+        ms = C.c_double()
+        _check(lib().pcas_profile_read(i, C.byref(n), C.byref(ms)))
+        out[name] = (int(n.value), float(ms.value))
+    return out
 
 
 def default_params(step_mm, **kw):
