@@ -117,6 +117,27 @@ int cost_grad(const float* f0, const float* mean, const float* U, int K, const d
               const float* y, const pcas_vol* vol, const pcas_cb* cb, double step_mm,
               double* J, double* dJdw, double* ab, void* ws, size_t ws_bytes, void* stream);
 
+/* cost_grad without a caller workspace: the paper has no counterpart.  For
+ * callers that cannot allocate device memory -- code recorded into a CUDA
+ * graph by stream capture, real-time loops where an allocation could stall,
+ * or host programs whose own allocator owns the device memory.  The scratch
+ * is a file-scope __device__ array of PCAS_STATIC_SCRATCH_BYTES (16 MiB) in
+ * the library, which every GPU that loads the library holds until exit; no
+ * call here allocates.  Volumes and detectors whose scratch
+ * (pcas_workspace_bytes) exceeds that size are rejected with
+ * PCAS_ERR_INVALID_ARG (e.g. up to 128x128x64 voxels with a 512x384
+ * detector fit; 256x256x100 does not).  The first call on each device looks
+ * up the array's device address (cudaGetSymbolAddress, which also loads the
+ * library's device code there): make that first call before any stream
+ * capture.  All calls on a device share the array and it keeps the last
+ * call's contents; each call clears what must start at zero.  Calls that
+ * overlap on the GPU (other streams, other host threads) race on it.
+ * Arguments, outputs and errors as cost_grad.  Synchronous. */
+#define PCAS_STATIC_SCRATCH_BYTES (16 * 1024 * 1024)
+int cost_grad_static(const float* f0, const float* mean, const float* U, int K, const double* w,
+                     const float* y, const pcas_vol* vol, const pcas_cb* cb, double step_mm,
+                     double* J, double* dJdw, double* ab, void* stream);
+
 /* Appendix: alternate Eq. (A.1) and Eq. (A.2) from w_init.  Each iteration
  * refits (a, b), takes d = -G/||G|| and tries mu = mu0, beta mu0, ... while
  * mu >= mu_min and at most max_trials times, accepting the first mu with

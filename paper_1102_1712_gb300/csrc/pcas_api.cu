@@ -532,6 +532,58 @@ int solve_projection(const float* f0, const float* mean, const float* U, int K, 
     return PCAS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// cost_grad_static: cost_grad for callers that cannot allocate device memory
+// (code running inside CUDA stream capture, real-time loops where allocation
+// is forbidden, or host programs whose allocator owns all device memory).  Its
+// scratch is the file-scope array below instead of a caller workspace.
+}  // extern "C"
+
+namespace {
+
+__device__ __align__(256) unsigned char g_static_scratch[PCAS_STATIC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 256;
+std::mutex g_static_mutex;
+void* g_static_addr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device, looked up once
+// per device.  In host code the symbol itself is only a host-side stand-in.
+int static_scratch(void** out) {
+    int dev = 0;
+    PCAS_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(PCAS_ERR_INVALID_ARG, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_static_mutex);
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        PCAS_CUDA(cudaGetSymbolAddress(&p, g_static_scratch));
+        g_static_addr[dev] = p;
+    }
+    *out = g_static_addr[dev];
+    return PCAS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cost_grad_static(const float* f0, const float* mean, const float* U, int K, const double* w,
+                     const float* y, const pcas_vol* vol, const pcas_cb* cb, double step_mm,
+                     double* J, double* dJdw, double* ab, void* stream) {
+    PCAS_TRY(check_vol(vol));
+    if (!cb || cb->nu < 1 || cb->nv < 1) return fail(PCAS_ERR_INVALID_ARG, "detector size invalid");
+    const size_t need = layout(vol, cb).total;
+    if (need > (size_t)PCAS_STATIC_SCRATCH_BYTES)
+        return fail(PCAS_ERR_INVALID_ARG,
+                    "cost_grad_static: this volume and detector need %zu bytes of scratch, more than the "
+                    "%d-byte static scratch; use cost_grad with a caller workspace",
+                    need, PCAS_STATIC_SCRATCH_BYTES);
+    void* scratch = nullptr;
+    PCAS_TRY(static_scratch(&scratch));
+    return cost_grad(f0, mean, U, K, w, y, vol, cb, step_mm, J, dJdw, ab, scratch,
+                     (size_t)PCAS_STATIC_SCRATCH_BYTES, stream);
+}
+
 int localize_tumor(const float* mean, const float* U, int K, const double* w, const pcas_vol* vol,
                    const double c_ref[3], int max_iter, double tol_mm, double c_out[3],
                    void* stream) {

@@ -68,6 +68,8 @@ _SIGS = {
     "drr_adjoint": (C.c_int, [_P, C.POINTER(Vol), C.POINTER(CB), C.c_double, _P, _P]),
     "cost_grad": (C.c_int, [_P, _P, _P, C.c_int, _D, _P, C.POINTER(Vol), C.POINTER(CB), C.c_double,
                             _D, _D, _D, _P, C.c_size_t, _P]),
+    "cost_grad_static": (C.c_int, [_P, _P, _P, C.c_int, _D, _P, C.POINTER(Vol), C.POINTER(CB),
+                                   C.c_double, _D, _D, _D, _P]),
     "solve_projection": (C.c_int, [_P, _P, _P, C.c_int, _P, C.POINTER(Vol), C.POINTER(CB), _D,
                                    C.POINTER(Params), _D, C.POINTER(Stats), _P, C.c_size_t, _P]),
     "localize_tumor": (C.c_int, [_P, _P, C.c_int, _D, C.POINTER(Vol), _D, C.c_int, C.c_double, _D, _P]),
@@ -247,6 +249,25 @@ def cost_grad(f0, mean, U, w, y, vol, cb, step, ws: Workspace = None, stream=Non
                            wv.ctypes.data_as(_D), _dev(y, "y", g.nu * g.nv), C.byref(vol_struct(vol)),
                            C.byref(g), float(step), C.byref(J), G.ctypes.data_as(_D),
                            ab.ctypes.data_as(_D), ws.ptr, ws.nbytes, _stream(stream)))
+    return J.value, G, (ab[0], ab[1])
+
+
+def cost_grad_static(f0, mean, U, w, y, vol, cb, step, stream=None):
+    """cost_grad without a workspace, for callers that cannot allocate device
+    memory: the library's fixed 16 MiB device scratch is used instead (see
+    include/pcasolve.h for the size limit and the sharing rules).
+    Returns (J, dJ/dw (K,), (a, b))."""
+    N = _nvox(vol)
+    K = _K(U, vol)
+    g = cb_struct(cb)
+    wv = _host_d(w, K)
+    J = C.c_double()
+    G = np.zeros(K)
+    ab = np.zeros(2)
+    _check(lib().cost_grad_static(_dev(f0, "f0", N), _dev(mean, "mean", 3 * N), _dev(U, "U"), K,
+                                  wv.ctypes.data_as(_D), _dev(y, "y", g.nu * g.nv), C.byref(vol_struct(vol)),
+                                  C.byref(g), float(step), C.byref(J), G.ctypes.data_as(_D),
+                                  ab.ctypes.data_as(_D), _stream(stream)))
     return J.value, G, (ab[0], ab[1])
 
 
