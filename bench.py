@@ -139,8 +139,8 @@ def kernel_bytes(N, M, K, has_mean):
     return {
         "warp_pca": model + 4 * N + 4 * N,           # model read, f0 read once, f written
         "drr_solver": 4 * N + 4 * M + 4 * M,         # f read once, y read, p written
-        "resid": 4 * M + 4 * M + 16 * M,             # p, y read; ray table written
-        "adjoint_grad": model + 4 * N + 16 * M,      # model + f0 re-read; ray table read
+        "resid": 4 * M + 4 * M + 32 * M,             # p, y read; ray table written
+        "adjoint_grad": model + 4 * N + 32 * M,      # model + f0 re-read; ray table read
     }
 
 
@@ -148,10 +148,13 @@ KERNEL_FILE = {"warp_pca": "k_warp_pca", "drr_solver": "k_drr_solver", "resid": 
                "adjoint_grad": "k_adjoint_grad"}
 
 
-def kernel_source_hash():
+KERNEL_SOURCES = {"warp_pca": ("pcas_warp.cu", "pcas_internal.cuh")}
+
+
+def kernel_source_hash(kernel):
     import hashlib
     h = hashlib.sha256()
-    for f in ("pcas_project.cu", "pcas_internal.cuh"):
+    for f in KERNEL_SOURCES.get(kernel, ("pcas_project.cu", "pcas_internal.cuh")):
         h.update(open(os.path.join(ROOT, "paper_1102_1712_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -166,7 +169,7 @@ def ncu_traffic(kernel):
         return None
     fields = dict(line.split(":", 1) for line in text.splitlines()
                   if line.startswith(("kernel_source_sha256_16:", "traffic_bytes_per_launch:")))
-    if fields.get("kernel_source_sha256_16", "").strip() != kernel_source_hash():
+    if fields.get("kernel_source_sha256_16", "").strip() != kernel_source_hash(kernel):
         return None
     try:
         return int(fields["traffic_bytes_per_launch"])

@@ -164,7 +164,7 @@ Layout layout(const pcas_vol* vol, const pcas_cb* cb) {
     L.fpad = off; off += align256((size_t)pd.px * pd.pny * pd.pnz * sizeof(float));
     L.p0 = off; off += align256(M * sizeof(float));
     L.p1 = off; off += align256(M * sizeof(float));
-    L.rayt = off; off += align256(M * sizeof(float4));
+    L.rayt = off; off += align256(2 * M * sizeof(float4));     // (step, r) and (1/step, 0) per ray
     L.part_drr = off; off += align256((size_t)drr_blocks(cb->nu, cb->nv) * NMOM * sizeof(double));
     L.part_res = off; off += align256((size_t)resid_blocks(cb->nu, cb->nv) * sizeof(double));
     L.part_adj = off; off += align256((size_t)ADJ_MAX_BLOCKS * PCAS_KMAX * sizeof(double));

@@ -60,8 +60,8 @@ def test_workspace_bytes_host_only(lib):
     cb = S.cone_beam(512, 384, 0.776, 0.776)
     n = P.workspace_bytes(vol, cb, 3)
     pad = (((256 + 5) + 3) // 4 * 4) * 258 * 102 * 4
-    assert n >= pad + 512 * 384 * (4 + 4 + 16) and n % 256 == 0
-    assert n < pad + 512 * 384 * 24 + 2_000_000
+    assert n >= pad + 512 * 384 * (4 + 4 + 32) and n % 256 == 0
+    assert n < pad + 512 * 384 * 40 + 2_000_000
     assert P.workspace_bytes(vol, cb, 0) == 0 and P.workspace_bytes(vol, cb, 9) == 0
 
 
