@@ -138,17 +138,20 @@ def kernel_bytes(N, M, K, has_mean):
     model = 12 * K * N + (12 * N if has_mean else 0)
     return {
         "warp_pca": model + 4 * N + 4 * N,           # model read, f0 read once, f written
+        "warp_batch": model + 4 * N + 16 * N,        # model + f0 once, four candidate volumes written
         "drr_solver": 4 * N + 4 * M + 4 * M,         # f read once, y read, p written
+        "drr_batch": 16 * N + 4 * M + 16 * M,        # four volumes read once, y read, four p written
         "resid": 4 * M + 4 * M + 32 * M,             # p, y read; ray table written
         "adjoint_grad": model + 4 * N + 32 * M,      # model + f0 re-read; ray table read
     }
 
 
-KERNEL_FILE = {"warp_pca": "k_warp_pca", "drr_solver": "k_drr_solver", "resid": "k_resid",
-               "adjoint_grad": "k_adjoint_grad"}
+KERNEL_FILE = {"warp_pca": "k_warp_pca", "warp_batch": "k_warp_batch", "drr_solver": "k_drr_solver",
+               "drr_batch": "k_drr_solver_batch", "resid": "k_resid", "adjoint_grad": "k_adjoint_grad"}
 
 
-KERNEL_SOURCES = {"warp_pca": ("pcas_warp.cu", "pcas_internal.cuh")}
+KERNEL_SOURCES = {"warp_pca": ("pcas_warp.cu", "pcas_internal.cuh"),
+                  "warp_batch": ("pcas_warp.cu", "pcas_internal.cuh")}
 
 
 def kernel_source_hash(kernel):
@@ -298,7 +301,7 @@ def run_ours(args, ws_, rank, local):
     pk, pk_kind = peaks()
     kb = kernel_bytes(N, M, K, False)
     kernels = {}
-    for name in ("warp_pca", "drr_solver", "resid", "adjoint_grad"):
+    for name in ("warp_pca", "warp_batch", "drr_solver", "drr_batch", "resid", "adjoint_grad"):
         n, tot = prof[name]
         if n:
             avg = tot / n
@@ -342,8 +345,10 @@ def run_ours(args, ws_, rank, local):
         "solver": {"iters_mean": round(float(iters.mean()), 3), "evals_mean": round(float(evals.mean()), 3)},
         "e2e": {"value": round(ws_ * K_ / te_s, 3), "unit": "projections/s",
                 "h2d_bytes_per_step": 4 * M,
-                # solver state read back at the end (488 B), one 4-byte flag per trial, 32 B of centroid
-                "d2h_bytes_per_step": int(round(488 + 4 * (float(evals.mean()) - 1) + 32))},
+                # solver state read back at the end (848 B), one 4-byte flag per batch of
+                # candidates (one per trial-projection launch), 32 B of centroid
+                "d2h_bytes_per_step": int(round(848 + 32 + 4 * (prof["drr_solver"][0] + prof["drr_batch"][0]
+                                                                - K_) / K_))},
     }
     if ws_ == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(vol, f0, c_ref, U, trace, train, angles, ys, W_)

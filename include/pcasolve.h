@@ -125,8 +125,8 @@ int cost_grad(const float* f0, const float* mean, const float* U, int K, const d
  * the library, which every GPU that loads the library holds until exit; no
  * call here allocates.  Volumes and detectors whose scratch
  * (pcas_workspace_bytes) exceeds that size are rejected with
- * PCAS_ERR_INVALID_ARG (e.g. up to 128x128x64 voxels with a 512x384
- * detector fit; 256x256x100 does not).  The first call on each device looks
+ * PCAS_ERR_INVALID_ARG (e.g. 96x96x48 voxels with a 256x192 detector fit;
+ * 256x256x100 does not).  The first call on each device looks
  * up the array's device address (cudaGetSymbolAddress, which also loads the
  * library's device code there): make that first call before any stream
  * capture.  All calls on a device share the array and it keeps the last
@@ -144,7 +144,11 @@ int cost_grad_static(const float* f0, const float* mean, const float* U, int K, 
  * J(w + mu d) <= J(w) - alpha mu ||G||; if none passes, no step is taken and
  * the solve ends.  It also ends after max_iter iterations or at G = 0.
  * f0, mean, U, y, ws: device; w_init, w_out (K), params, stats: host.
- * Synchronous (one host read of a 4-byte flag per trial step). */
+ * The backtracking candidates are evaluated up to four at a time (one warp and
+ * one projection pass for all of them) and tested in schedule order, so the
+ * accepted step is the one the one-at-a-time rule would take; stats->evals
+ * counts evaluations as that rule would.  Synchronous (one host read of a
+ * 4-byte flag per batch of candidates). */
 int solve_projection(const float* f0, const float* mean, const float* U, int K, const float* y,
                      const pcas_vol* vol, const pcas_cb* cb, const double* w_init,
                      const pcas_params* params, double* w_out, pcas_stats* stats, void* ws,
@@ -188,7 +192,9 @@ enum {
     PCAS_K_WARP_DVF = 7,     /* warp_volume                                     */
     PCAS_K_LOCALIZE = 8,     /* localize_tumor                                  */
     PCAS_K_INIT = 9,         /* solver state reset                              */
-    PCAS_K_COUNT = 10
+    PCAS_K_WARP_BATCH = 10,  /* four line-search candidates warped at once      */
+    PCAS_K_DRR_BATCH = 11,   /* four candidates projected and tested at once    */
+    PCAS_K_COUNT = 12
 };
 int pcas_profile(int on);
 int pcas_profile_read(int kind, long long* launches, double* total_ms);

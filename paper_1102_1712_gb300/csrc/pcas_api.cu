@@ -152,20 +152,21 @@ int check_model(const float* mean, const float* U, int K) {
 
 // ------------------------------------------------------------- workspace
 struct Layout {
-    size_t state, fpad, p0, p1, rayt, part_drr, part_res, part_adj, total;
+    size_t state, fpad, fpad4, pbuf, rayt, part_drr, part_res, part_adj, total;
 };
 
 Layout layout(const pcas_vol* vol, const pcas_cb* cb) {
     Layout L;
     Pad pd = make_pad(vol->nx, vol->ny, vol->nz);
+    const size_t npad = (size_t)pd.px * pd.pny * pd.pnz;
     size_t M = (size_t)cb->nu * cb->nv;
     size_t off = 0;
     L.state = off; off += align256(sizeof(SolveState));
-    L.fpad = off; off += align256((size_t)pd.px * pd.pny * pd.pnz * sizeof(float));
-    L.p0 = off; off += align256(M * sizeof(float));
-    L.p1 = off; off += align256(M * sizeof(float));
-    L.rayt = off; off += align256(2 * M * sizeof(float4));     // (step, r) and (1/step, 0) per ray
-    L.part_drr = off; off += align256((size_t)drr_blocks(cb->nu, cb->nv) * NMOM * sizeof(double));
+    L.fpad = off; off += align256(npad * sizeof(float));                 // f(w), zero halo
+    L.fpad4 = off; off += align256(npad * sizeof(float4));               // four candidates
+    L.pbuf = off; off += align256((size_t)NBUF * M * sizeof(float));     // projection ring
+    L.rayt = off; off += align256(2 * M * sizeof(float4));               // (step, r), (1/step, 0)
+    L.part_drr = off; off += align256((size_t)drr_blocks(cb->nu, cb->nv) * DRR_PART_VALS * sizeof(double));
     L.part_res = off; off += align256((size_t)resid_blocks(cb->nu, cb->nv) * sizeof(double));
     L.part_adj = off; off += align256((size_t)ADJ_MAX_BLOCKS * PCAS_KMAX * sizeof(double));
     L.total = off;
@@ -174,9 +175,10 @@ Layout layout(const pcas_vol* vol, const pcas_cb* cb) {
 
 struct Ws {
     SolveState* st;
-    float *fpad, *p0, *p1;
-    float4* rayt;
+    float *fpad, *pbuf;
+    float4 *fpad4, *rayt;
     double *part_drr, *part_res, *part_adj;
+    size_t fpad_bytes, fpad4_bytes;
 };
 
 int bind_ws(void* ws, size_t ws_bytes, const pcas_vol* vol, const pcas_cb* cb, Ws* W) {
@@ -188,12 +190,14 @@ int bind_ws(void* ws, size_t ws_bytes, const pcas_vol* vol, const pcas_cb* cb, W
     char* b = static_cast<char*>(ws);
     W->st = reinterpret_cast<SolveState*>(b + L.state);
     W->fpad = reinterpret_cast<float*>(b + L.fpad);
-    W->p0 = reinterpret_cast<float*>(b + L.p0);
-    W->p1 = reinterpret_cast<float*>(b + L.p1);
+    W->fpad4 = reinterpret_cast<float4*>(b + L.fpad4);
+    W->pbuf = reinterpret_cast<float*>(b + L.pbuf);
     W->rayt = reinterpret_cast<float4*>(b + L.rayt);
     W->part_drr = reinterpret_cast<double*>(b + L.part_drr);
     W->part_res = reinterpret_cast<double*>(b + L.part_res);
     W->part_adj = reinterpret_cast<double*>(b + L.part_adj);
+    W->fpad_bytes = L.fpad4 - L.fpad;
+    W->fpad4_bytes = L.pbuf - L.fpad4;
     return PCAS_OK;
 }
 
@@ -270,13 +274,14 @@ __global__ void k_init_state(SolveState* st, int K, double w0, double w1, double
     const double w[PCAS_KMAX] = {w0, w1, w2, w3, w4, w5, w6, w7};
     for (int k = 0; k < PCAS_KMAX; k++) {
         st->w[k] = k < K ? w[k] : 0.0;
-        st->wt[k] = st->w[k];
         st->d[k] = 0.0;
         st->G[k] = 0.0;
+        for (int j = 0; j < TRIAL_BATCH; j++) st->wt[j][k] = st->w[k];
     }
+    for (int j = 0; j < TRIAL_BATCH; j++) st->mu_batch[j] = 0.0;
     st->gnorm = st->a = st->b = st->J = st->J0 = st->Jt = 0.0;
     st->mu = mu0;
-    for (int i = 0; i < 2; i++)
+    for (int i = 0; i < NBUF; i++)
         for (int j = 0; j < NMOM; j++) st->mom[i][j] = 0.0;
     st->mu0 = mu0; st->alpha = alpha; st->beta = beta; st->mu_min = mu_min;
     st->K = K; st->max_trials = max_trials;
@@ -324,8 +329,8 @@ int eval_gradient_pipeline(const float* f0, const float* mean, const float* U, i
     ws.phase = &W.st->phase;
     PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, K, ws, g, pd, W.fpad, s));
     PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
-                launch_drr_solver(W.fpad, g, pd, V, y, W.p0, W.p1, 0, W.st, W.part_drr, s));
-    PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.p0, W.p1, y, V, 1, W.rayt, W.st, W.part_res, s));
+                launch_drr_solver(W.fpad, W.fpad4, g, pd, V, y, W.pbuf, 0, 1, W.st, W.part_drr, s));
+    PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, 1, W.rayt, W.st, W.part_res, s));
     PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
                 launch_adjoint_grad(W.rayt, g, V, f0, mean, U, K, step_setup, W.st, W.part_adj,
                                     adjoint_block_cap(), s));
@@ -449,7 +454,7 @@ int cost_grad(const float* f0, const float* mean, const float* U, int K, const d
     cudaStream_t s = as_stream(stream);
     Grid g = make_grid(vol);
     Pad pd = make_pad(vol->nx, vol->ny, vol->nz);
-    PCAS_CUDA(cudaMemsetAsync(W.fpad, 0, (size_t)pd.px * pd.pny * pd.pnz * sizeof(float), s));
+    PCAS_CUDA(cudaMemsetAsync(W.fpad, 0, W.fpad_bytes, s));
     PCAS_TRY(launch_init(W.st, K, w, nullptr, s));
     PCAS_TRY(eval_gradient_pipeline(f0, mean, U, K, y, g, pd, V, W, 0, s));
     SolveState h;
@@ -486,30 +491,57 @@ int solve_projection(const float* f0, const float* mean, const float* U, int K, 
     Grid g = make_grid(vol);
     Pad pd = make_pad(vol->nx, vol->ny, vol->nz);
     const int adj_cap = adjoint_block_cap();
-    PCAS_CUDA(cudaMemsetAsync(W.fpad, 0, (size_t)pd.px * pd.pny * pd.pnz * sizeof(float), s));
+    PCAS_CUDA(cudaMemsetAsync(W.fpad, 0, W.fpad_bytes + W.fpad4_bytes, s));   // zero halos
     PCAS_TRY(launch_init(W.st, K, w_init, prm, s));
     WSrc wcur{}, wtrial{};
     wcur.dev = W.st->w;
     wcur.phase = &W.st->phase;
-    wtrial.dev = W.st->wt;
+    wtrial.dev = W.st->wt[0];
     wtrial.phase = &W.st->phase;
     PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, K, wcur, g, pd, W.fpad, s));
     PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
-                launch_drr_solver(W.fpad, g, pd, V, y, W.p0, W.p1, 0, W.st, W.part_drr, s));
+                launch_drr_solver(W.fpad, W.fpad4, g, pd, V, y, W.pbuf, 0, 1, W.st, W.part_drr, s));
     int iters = 0, phase = PH_RUNNING;
     for (int it = 0; it < prm->max_iter; it++) {
-        PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.p0, W.p1, y, V, it == 0, W.rayt, W.st, W.part_res, s));
+        PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, it == 0, W.rayt, W.st, W.part_res, s));
         PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
                     launch_adjoint_grad(W.rayt, g, V, f0, mean, U, K, 1, W.st, W.part_adj, adj_cap, s));
-        // Armijo backtracking: each trial renders w + mu d and tests it on device;
-        // the host only reads the phase flag to decide whether to go on.
-        for (int tr = 0; tr <= prm->max_trials; tr++) {
-            PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, K, wtrial, g, pd, W.fpad, s));
-            PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
-                        launch_drr_solver(W.fpad, g, pd, V, y, W.p0, W.p1, 1, W.st, W.part_drr, s));
+        // Armijo backtracking over the schedule mu0, beta mu0, ...: the next (up
+        // to four) step sizes that the rule may still try are rendered and
+        // tested in one pass; the device accepts the first that passes, in
+        // order.  The host mirrors the schedule only to size each batch, and
+        // reads one flag per batch.
+        double mu_t = prm->mu0;
+        int t = 0;
+        phase = PH_RUNNING;
+        while (true) {
+            int nvalid = 0;
+            double m = mu_t;
+            while (nvalid < TRIAL_BATCH && m >= prm->mu_min && t + nvalid < prm->max_trials) {
+                nvalid++;
+                m *= prm->beta;
+            }
+            if (nvalid == 0) {          // nothing left to try: the device has stopped too
+                PCAS_CUDA(cudaMemcpyAsync(&phase, &W.st->phase, sizeof(int), cudaMemcpyDeviceToHost, s));
+                PCAS_CUDA(cudaStreamSynchronize(s));
+                if (phase == PH_RUNNING) phase = PH_STOP;
+                break;
+            }
+            if (nvalid >= 2) {
+                PCAS_LAUNCH(PCAS_K_WARP_BATCH, s, launch_warp_batch(f0, mean, U, K, W.st, g, pd, W.fpad4, s));
+                PCAS_LAUNCH(PCAS_K_DRR_BATCH, s,
+                            launch_drr_solver(W.fpad, W.fpad4, g, pd, V, y, W.pbuf, TRIAL_BATCH, nvalid,
+                                              W.st, W.part_drr, s));
+            } else {
+                PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, K, wtrial, g, pd, W.fpad, s));
+                PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
+                            launch_drr_solver(W.fpad, W.fpad4, g, pd, V, y, W.pbuf, 1, 1, W.st, W.part_drr, s));
+            }
             PCAS_CUDA(cudaMemcpyAsync(&phase, &W.st->phase, sizeof(int), cudaMemcpyDeviceToHost, s));
             PCAS_CUDA(cudaStreamSynchronize(s));
             if (phase != PH_RUNNING) break;
+            t += nvalid;
+            mu_t = m;
         }
         if (phase == PH_ACCEPT || phase == PH_STOP) iters++;
         if (phase != PH_ACCEPT) break;

@@ -29,21 +29,29 @@ struct Grid {
     float inv_sx, inv_sy, inv_sz;
 };
 
-// Internal warped-volume layout with a zero halo: voxel (i,j,k) lives at
-// ((k+1) pny + (j+1)) px + (i+4).  px is a multiple of 4 and >= nx + 5, so the
-// interior rows start 16-byte aligned and every tap of a sample clamped to
-// [-1, n] stays inside the allocation.
+// Internal warped-volume layout with a zero halo two voxels deep: voxel
+// (i,j,k) lives at element ((k+2) pny + (j+2)) px + (i+4).  px is a multiple of
+// 4 and >= nx + 6, so interior rows start 16-byte aligned, and every tap of a
+// sample within half a voxel of the support box [-1, n] lands inside the
+// allocation on a halo zero or a voxel: the ray march needs no clamps.
 struct Pad {
     int px, pny, pnz;
 };
 
 __host__ __device__ inline Pad make_pad(int nx, int ny, int nz) {
     Pad p;
-    p.px = ((nx + 5) + 3) & ~3;
-    p.pny = ny + 2;
-    p.pnz = nz + 2;
+    p.px = ((nx + 6) + 3) & ~3;
+    p.pny = ny + 4;
+    p.pnz = nz + 4;
     return p;
 }
+
+__host__ __device__ inline long pad_index(const Pad& pd, int i, int j, int k) {
+    return ((long)(k + 2) * pd.pny + (j + 2)) * pd.px + (i + 4);
+}
+
+// Trial step sizes evaluated together in one warp + projection pass.
+enum { TRIAL_BATCH = 4, NBUF = TRIAL_BATCH + 1 };
 
 // ----------------------------------------------------------- solver state
 enum Phase : int {
@@ -57,15 +65,16 @@ enum Phase : int {
 enum { NMOM = 6 };      // Sp, Syp, Spp, Srr, Sy, Syy
 
 struct SolveState {
-    double w[PCAS_KMAX], wt[PCAS_KMAX], d[PCAS_KMAX], G[PCAS_KMAX];
+    double w[PCAS_KMAX], d[PCAS_KMAX], G[PCAS_KMAX];
+    double wt[TRIAL_BATCH][PCAS_KMAX];    // candidate coefficients w + mu_j d of the batch
+    double mu_batch[TRIAL_BATCH];         // their step sizes, in the backtracking order
     double gnorm, a, b, J, J0, Jt, mu;
-    double mom[2][NMOM];            // final moments of the two projection buffers
+    double mom[NBUF][NMOM];               // final moments of the projection buffers
     double mu0, alpha, beta, mu_min;
     int K, max_trials;
-    int cur;                        // buffer holding P f(w)
+    int cur;                              // buffer holding P f(w)
     int phase, evals, trials;
-    unsigned int counter[4];        // last-block counters (reset by the last block)
-    int pad_[2];
+    unsigned int counter[4];              // last-block counters (reset by the last block)
 };
 
 // Reduction scratch: per-block partials plus the counter used to find the
@@ -117,25 +126,43 @@ __device__ __forceinline__ float tri_dense(const float* __restrict__ f, const Gr
     return fmaf(zz, c1 - c0, c0);
 }
 
-// Same interpolant on the zero-halo layout: no bounds tests.  The floor is
-// clamped to [-1, n-1] and the fraction to [0, 1]; for q in [-1, n] this is
-// the same value (the clamped cases land on halo zeros with full weight).
-__device__ __forceinline__ float tri_padded(const float* __restrict__ f, const Grid& g,
-                                            const Pad& pd, float qx, float qy, float qz) {
-    float fx = fminf(fmaxf(floorf(qx), -1.0f), (float)(g.nx - 1));
-    float fy = fminf(fmaxf(floorf(qy), -1.0f), (float)(g.ny - 1));
-    float fz = fminf(fmaxf(floorf(qz), -1.0f), (float)(g.nz - 1));
-    float zx = __saturatef(qx - fx), zy = __saturatef(qy - fy), zz = __saturatef(qz - fz);
+// Same interpolant on the zero-halo layout: no bounds tests and no clamps.
+// Valid for q within half a voxel of [-1, n] (the caller guarantees it): the
+// floor is then in [-2, n] and every tap is a voxel or a halo zero.
+__device__ __forceinline__ float tri_padded(const float* __restrict__ f, const Pad& pd, float qx,
+                                            float qy, float qz) {
+    const float fx = floorf(qx), fy = floorf(qy), fz = floorf(qz);
+    const float zx = qx - fx, zy = qy - fy, zz = qz - fz;
     const int sy = pd.px, sz = pd.px * pd.pny;
-    const float* b = f + ((int)fz + 1) * sz + ((int)fy + 1) * sy + ((int)fx + 4);
-    float v000 = __ldg(b), v100 = __ldg(b + 1);
-    float v010 = __ldg(b + sy), v110 = __ldg(b + sy + 1);
-    float v001 = __ldg(b + sz), v101 = __ldg(b + sz + 1);
-    float v011 = __ldg(b + sz + sy), v111 = __ldg(b + sz + sy + 1);
-    float c00 = fmaf(zx, v100 - v000, v000), c10 = fmaf(zx, v110 - v010, v010);
-    float c01 = fmaf(zx, v101 - v001, v001), c11 = fmaf(zx, v111 - v011, v011);
-    float c0 = fmaf(zy, c10 - c00, c00), c1 = fmaf(zy, c11 - c01, c01);
+    const float* b = f + (((int)fz + 2) * sz + ((int)fy + 2) * sy + ((int)fx + 4));
+    const float v000 = __ldg(b), v100 = __ldg(b + 1);
+    const float v010 = __ldg(b + sy), v110 = __ldg(b + sy + 1);
+    const float v001 = __ldg(b + sz), v101 = __ldg(b + sz + 1);
+    const float v011 = __ldg(b + sz + sy), v111 = __ldg(b + sz + sy + 1);
+    const float c00 = fmaf(zx, v100 - v000, v000), c10 = fmaf(zx, v110 - v010, v010);
+    const float c01 = fmaf(zx, v101 - v001, v001), c11 = fmaf(zx, v111 - v011, v011);
+    const float c0 = fmaf(zy, c10 - c00, c00), c1 = fmaf(zy, c11 - c01, c01);
     return fmaf(zz, c1 - c0, c0);
+}
+
+__device__ __forceinline__ float lerp1(float z, float a, float b) { return fmaf(z, b - a, a); }
+__device__ __forceinline__ float4 lerp4(float z, const float4& a, const float4& b) {
+    return make_float4(lerp1(z, a.x, b.x), lerp1(z, a.y, b.y), lerp1(z, a.z, b.z), lerp1(z, a.w, b.w));
+}
+
+// Four interleaved volumes (one float4 per voxel) sampled at the same point:
+// the weights are computed once, the eight taps are 16-byte loads.
+__device__ __forceinline__ float4 tri_padded4(const float4* __restrict__ f, const Pad& pd, float qx,
+                                              float qy, float qz) {
+    const float fx = floorf(qx), fy = floorf(qy), fz = floorf(qz);
+    const float zx = qx - fx, zy = qy - fy, zz = qz - fz;
+    const int sy = pd.px, sz = pd.px * pd.pny;
+    const float4* b = f + (((int)fz + 2) * sz + ((int)fy + 2) * sy + ((int)fx + 4));
+    const float4 c00 = lerp4(zx, __ldg(b), __ldg(b + 1));
+    const float4 c10 = lerp4(zx, __ldg(b + sy), __ldg(b + sy + 1));
+    const float4 c01 = lerp4(zx, __ldg(b + sz), __ldg(b + sz + 1));
+    const float4 c11 = lerp4(zx, __ldg(b + sz + sy), __ldg(b + sz + sy + 1));
+    return lerp4(zz, lerp4(zy, c00, c10), lerp4(zy, c01, c11));
 }
 
 // ----------------------------------------------------------------- rays
@@ -254,14 +281,20 @@ struct WSrc {                 // where a PCA-model kernel takes w from
 cudaError_t launch_pca_dvf(const float* mean, const float* U, int K, const float* w, Grid g,
                            float* dvf, cudaStream_t s);
 cudaError_t launch_warp_dvf(const float* f0, const float* dvf, Grid g, float* f, cudaStream_t s);
+// Solver warp: S = 1 writes f(w_src) to the scalar zero-halo buffer; S = 4
+// writes the four candidate volumes st->wt[0..3] interleaved (float4).
 cudaError_t launch_warp_pca(const float* f0, const float* mean, const float* U, int K, WSrc w,
                             Grid g, Pad pd, float* fpad, cudaStream_t s);
+cudaError_t launch_warp_batch(const float* f0, const float* mean, const float* U, int K,
+                              const SolveState* st, Grid g, Pad pd, float4* fpad4, cudaStream_t s);
 cudaError_t launch_drr_plain(const float* f, Grid g, const View& V, float* p, cudaStream_t s);
-cudaError_t launch_drr_solver(const float* fpad, Grid g, Pad pd, const View& V, const float* y,
-                              float* p0, float* p1, int trial, SolveState* st, double* part,
-                              cudaStream_t s);
-cudaError_t launch_resid(const float* p0, const float* p1, const float* y, const View& V,
-                         int first, float4* rayt, SolveState* st, double* part, cudaStream_t s);
+// Solver projector.  mode 0: first evaluation into buffer cur; mode 1: one
+// trial volume; mode 4: the four-volume batch (nvalid of them on the schedule).
+cudaError_t launch_drr_solver(const float* fpad, const float4* fpad4, Grid g, Pad pd,
+                              const View& V, const float* y, float* pbuf, int mode, int nvalid,
+                              SolveState* st, double* part, cudaStream_t s);
+cudaError_t launch_resid(const float* pbuf, const float* y, const View& V, int first, float4* rayt,
+                         SolveState* st, double* part, cudaStream_t s);
 cudaError_t launch_adjoint_plain(const float* img, Grid g, const View& V, float* gout,
                                  cudaStream_t s);
 cudaError_t launch_adjoint_grad(const float4* rayt, Grid g, const View& V, const float* f0,
@@ -273,6 +306,7 @@ cudaError_t launch_localize(const float* mean, const float* U, int K, const doub
 
 // Number of partial slots each solver kernel needs (sizes the workspace).
 inline unsigned drr_blocks(int nu, int nv) { return (unsigned)((nu + 7) / 8) * ((nv + 15) / 16); }
+enum { DRR_PART_VALS = 4 * TRIAL_BATCH + 2 };   // per-volume Sp, Syp, Spp, Srr + Sy, Syy
 inline unsigned resid_blocks(int nu, int nv) { return (unsigned)(((long)nu * nv + 255) / 256); }
 enum { ADJ_MAX_BLOCKS = 4096 };
 

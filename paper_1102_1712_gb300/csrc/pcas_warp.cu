@@ -100,8 +100,7 @@ k_warp_pca(const float* __restrict__ f0, const float* __restrict__ mean,
         for (int e = 0; e < 4; e++)
             o[e] = tri_dense(f0, g, fmaf(x[0][e], g.inv_sx, (float)(i + e)),
                              fmaf(x[1][e], g.inv_sy, (float)j), fmaf(x[2][e], g.inv_sz, (float)k));
-        float* dst = fpad + ((long)(k + 1) * pd.pny + (j + 1)) * pd.px + (i + 4);
-        *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+        *reinterpret_cast<float4*>(fpad + pad_index(pd, i, j, k)) = make_float4(o[0], o[1], o[2], o[3]);
     } else {
         if (t >= N) return;
         int i = (int)(t % g.nx);
@@ -113,10 +112,54 @@ k_warp_pca(const float* __restrict__ f0, const float* __restrict__ mean,
             for (int kk = 0; kk < K; kk++) v = fmaf(s_w[kk], U[((long)kk * 3 + c) * N + t], v);
             x[c] = v;
         }
-        fpad[((long)(k + 1) * pd.pny + (j + 1)) * pd.px + (i + 4)] =
+        fpad[pad_index(pd, i, j, k)] =
             tri_dense(f0, g, fmaf(x[0], g.inv_sx, (float)i), fmaf(x[1], g.inv_sy, (float)j),
                       fmaf(x[2], g.inv_sz, (float)k));
     }
+}
+
+// Four candidate volumes of the line search at once (Eq. 1 + A.5 for each
+// w + mu_j d): the motion model is read once per voxel and reused for the four
+// coefficient vectors; each DVF is formed in the same operation order as the
+// single-volume warp, so a candidate's volume is bit-identical to a lone
+// evaluation.  Output: one float4 (f_0..f_3) per voxel, zero-halo layout.
+__global__ void __launch_bounds__(kWarpThreads)
+k_warp_batch(const float* __restrict__ f0, const float* __restrict__ mean,
+             const float* __restrict__ U, int K, const SolveState* st, Grid g, Pad pd, long N,
+             float4* __restrict__ fpad4) {
+    if (st->phase >= PH_STOP) return;
+    __shared__ float s_w[TRIAL_BATCH][PCAS_KMAX];
+    if (threadIdx.x < TRIAL_BATCH * PCAS_KMAX) {
+        const int j = threadIdx.x / PCAS_KMAX, k = threadIdx.x % PCAS_KMAX;
+        s_w[j][k] = k < K ? (float)st->wt[j][k] : 0.0f;
+    }
+    __syncthreads();
+    const long n = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int i = (int)(n % g.nx);
+    const long r = n / g.nx;
+    const int j = (int)(r % g.ny), k = (int)(r / g.ny);
+    float x[TRIAL_BATCH][3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const float m = mean ? __ldcs(mean + c * N + n) : 0.0f;
+#pragma unroll
+        for (int b = 0; b < TRIAL_BATCH; b++) x[b][c] = m;
+    }
+    for (int kk = 0; kk < K; kk++) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const float u = __ldcs(U + ((long)kk * 3 + c) * N + n);
+#pragma unroll
+            for (int b = 0; b < TRIAL_BATCH; b++) x[b][c] = fmaf(s_w[b][kk], u, x[b][c]);
+        }
+    }
+    float o[TRIAL_BATCH];
+#pragma unroll
+    for (int b = 0; b < TRIAL_BATCH; b++)
+        o[b] = tri_dense(f0, g, fmaf(x[b][0], g.inv_sx, (float)i), fmaf(x[b][1], g.inv_sy, (float)j),
+                         fmaf(x[b][2], g.inv_sz, (float)k));
+    fpad4[pad_index(pd, i, j, k)] = make_float4(o[0], o[1], o[2], o[3]);
 }
 
 inline bool aligned16(const void* p) { return p == nullptr || ((uintptr_t)p & 15u) == 0; }
@@ -148,6 +191,13 @@ cudaError_t launch_warp_pca(const float* f0, const float* mean, const float* U, 
     bool vec = (g.nx % 4 == 0) && aligned16(mean) && aligned16(U) && aligned16(fpad);
     if (vec) k_warp_pca<true><<<blocks_for(N / 4), kWarpThreads, 0, s>>>(f0, mean, U, K, w, g, pd, N, fpad);
     else k_warp_pca<false><<<blocks_for(N), kWarpThreads, 0, s>>>(f0, mean, U, K, w, g, pd, N, fpad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_warp_batch(const float* f0, const float* mean, const float* U, int K,
+                              const SolveState* st, Grid g, Pad pd, float4* fpad4, cudaStream_t s) {
+    long N = (long)g.nx * g.ny * g.nz;
+    k_warp_batch<<<blocks_for(N), kWarpThreads, 0, s>>>(f0, mean, U, K, st, g, pd, N, fpad4);
     return cudaGetLastError();
 }
 

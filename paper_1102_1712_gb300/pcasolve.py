@@ -81,7 +81,7 @@ _SIGS = {
 
 # kernel classes of pcas_profile_read (include/pcasolve.h)
 KERNELS = ["warp_pca", "drr_solver", "resid", "adjoint_grad", "drr_forward", "drr_adjoint",
-           "pca_dvf", "warp_volume", "localize", "init"]
+           "pca_dvf", "warp_volume", "localize", "init", "warp_batch", "drr_batch"]
 
 
 def lib():
