@@ -152,10 +152,11 @@ int check_model(const float* mean, const float* U, int K) {
 
 // ------------------------------------------------------------- workspace
 struct Layout {
-    size_t state, fpad, fpad4, pbuf, rayt, part_drr, part_res, part_adj, total;
+    size_t state, fpad, fpad4, pbuf, rayt, part_drr, part_res, part_adj, act_idx, act_h, tile_count,
+        tile_off, total;
 };
 
-Layout layout(const pcas_vol* vol, const pcas_cb* cb) {
+Layout layout(const pcas_vol* vol, const pcas_cb* cb, int K) {
     Layout L;
     Pad pd = make_pad(vol->nx, vol->ny, vol->nz);
     const size_t npad = (size_t)pd.px * pd.pny * pd.pnz;
@@ -169,6 +170,11 @@ Layout layout(const pcas_vol* vol, const pcas_cb* cb) {
     L.part_drr = off; off += align256((size_t)drr_blocks(cb->nu, cb->nv) * DRR_PART_VALS * sizeof(double));
     L.part_res = off; off += align256((size_t)resid_blocks(cb->nu, cb->nv) * sizeof(double));
     L.part_adj = off; off += align256((size_t)ADJ_MAX_BLOCKS * PCAS_KMAX * sizeof(double));
+    const size_t nt = (size_t)adj_tiles(vol->nx, vol->ny, vol->nz), cap = nt * 256;
+    L.act_idx = off; off += align256(cap * sizeof(int));                  // compacted voxels
+    L.act_h = off; off += align256((size_t)K * cap * sizeof(float));
+    L.tile_count = off; off += align256(nt * sizeof(int));
+    L.tile_off = off; off += align256((nt + 1) * sizeof(int));
     L.total = off;
     return L;
 }
@@ -179,10 +185,11 @@ struct Ws {
     float4 *fpad4, *rayt;
     double *part_drr, *part_res, *part_adj;
     size_t fpad_bytes, fpad4_bytes;
+    AdjScratch adj;
 };
 
-int bind_ws(void* ws, size_t ws_bytes, const pcas_vol* vol, const pcas_cb* cb, Ws* W) {
-    Layout L = layout(vol, cb);
+int bind_ws(void* ws, size_t ws_bytes, const pcas_vol* vol, const pcas_cb* cb, int K, Ws* W) {
+    Layout L = layout(vol, cb, K);
     if (!ws) return fail(PCAS_ERR_INVALID_ARG, "workspace is NULL");
     if (((uintptr_t)ws & 255u) != 0) return fail(PCAS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
     if (ws_bytes < L.total)
@@ -196,6 +203,10 @@ int bind_ws(void* ws, size_t ws_bytes, const pcas_vol* vol, const pcas_cb* cb, W
     W->part_drr = reinterpret_cast<double*>(b + L.part_drr);
     W->part_res = reinterpret_cast<double*>(b + L.part_res);
     W->part_adj = reinterpret_cast<double*>(b + L.part_adj);
+    W->adj.act_idx = reinterpret_cast<int*>(b + L.act_idx);
+    W->adj.act_h = reinterpret_cast<float*>(b + L.act_h);
+    W->adj.tile_count = reinterpret_cast<int*>(b + L.tile_count);
+    W->adj.tile_off = reinterpret_cast<int*>(b + L.tile_off);
     W->fpad_bytes = L.fpad4 - L.fpad;
     W->fpad4_bytes = L.pbuf - L.fpad4;
     return PCAS_OK;
@@ -287,6 +298,8 @@ __global__ void k_init_state(SolveState* st, int K, double w0, double w1, double
     st->K = K; st->max_trials = max_trials;
     st->cur = 0; st->phase = PH_RUNNING; st->evals = 0; st->trials = 0;
     for (int i = 0; i < 4; i++) st->counter[i] = 0u;
+    for (int i = 0; i < 2; i++)
+        for (int j = 0; j < 6; j++) st->box[i][j] = BOX_EMPTY;
 }
 
 int launch_init(SolveState* st, int K, const double* w, const pcas_params* prm, cudaStream_t s) {
@@ -327,12 +340,12 @@ int eval_gradient_pipeline(const float* f0, const float* mean, const float* U, i
     WSrc ws{};
     ws.dev = W.st->w;
     ws.phase = &W.st->phase;
-    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, K, ws, g, pd, W.fpad, s));
+    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, K, ws, g, pd, W.fpad, W.st->box[0], s));
     PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
                 launch_drr_solver(W.fpad, W.fpad4, g, pd, V, y, W.pbuf, 0, 1, W.st, W.part_drr, s));
     PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, 1, W.rayt, W.st, W.part_res, s));
     PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
-                launch_adjoint_grad(W.rayt, g, V, f0, mean, U, K, step_setup, W.st, W.part_adj,
+                launch_adjoint_grad(W.rayt, g, V, f0, mean, U, K, step_setup, W.st, W.part_adj, W.adj,
                                     adjoint_block_cap(), s));
     return PCAS_OK;
 }
@@ -384,7 +397,7 @@ int pcas_version(void) { return PCAS_VERSION; }
 
 size_t pcas_workspace_bytes(const pcas_vol* vol, const pcas_cb* cb, int K) {
     if (check_vol(vol) != PCAS_OK || !cb || cb->nu < 1 || cb->nv < 1 || K < 1 || K > PCAS_KMAX) return 0;
-    return layout(vol, cb).total;
+    return layout(vol, cb, K).total;
 }
 
 int pca_dvf(const float* mean, const float* U, int K, const double* w, const pcas_vol* vol,
@@ -450,7 +463,7 @@ int cost_grad(const float* f0, const float* mean, const float* U, int K, const d
     View V;
     PCAS_TRY(make_view(vol, cb, step_mm, &V));
     Ws W;
-    PCAS_TRY(bind_ws(ws, ws_bytes, vol, cb, &W));
+    PCAS_TRY(bind_ws(ws, ws_bytes, vol, cb, K, &W));
     cudaStream_t s = as_stream(stream);
     Grid g = make_grid(vol);
     Pad pd = make_pad(vol->nx, vol->ny, vol->nz);
@@ -486,7 +499,7 @@ int solve_projection(const float* f0, const float* mean, const float* U, int K, 
     View V;
     PCAS_TRY(make_view(vol, cb, prm->step_mm, &V));
     Ws W;
-    PCAS_TRY(bind_ws(ws, ws_bytes, vol, cb, &W));
+    PCAS_TRY(bind_ws(ws, ws_bytes, vol, cb, K, &W));
     cudaStream_t s = as_stream(stream);
     Grid g = make_grid(vol);
     Pad pd = make_pad(vol->nx, vol->ny, vol->nz);
@@ -498,14 +511,14 @@ int solve_projection(const float* f0, const float* mean, const float* U, int K, 
     wcur.phase = &W.st->phase;
     wtrial.dev = W.st->wt[0];
     wtrial.phase = &W.st->phase;
-    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, K, wcur, g, pd, W.fpad, s));
+    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, K, wcur, g, pd, W.fpad, W.st->box[0], s));
     PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
                 launch_drr_solver(W.fpad, W.fpad4, g, pd, V, y, W.pbuf, 0, 1, W.st, W.part_drr, s));
     int iters = 0, phase = PH_RUNNING;
     for (int it = 0; it < prm->max_iter; it++) {
         PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, it == 0, W.rayt, W.st, W.part_res, s));
         PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
-                    launch_adjoint_grad(W.rayt, g, V, f0, mean, U, K, 1, W.st, W.part_adj, adj_cap, s));
+                    launch_adjoint_grad(W.rayt, g, V, f0, mean, U, K, 1, W.st, W.part_adj, W.adj, adj_cap, s));
         // Armijo backtracking over the schedule mu0, beta mu0, ...: the next (up
         // to four) step sizes that the rule may still try are rendered and
         // tested in one pass; the device accepts the first that passes, in
@@ -533,7 +546,7 @@ int solve_projection(const float* f0, const float* mean, const float* U, int K, 
                             launch_drr_solver(W.fpad, W.fpad4, g, pd, V, y, W.pbuf, TRIAL_BATCH, nvalid,
                                               W.st, W.part_drr, s));
             } else {
-                PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, K, wtrial, g, pd, W.fpad, s));
+                PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, K, wtrial, g, pd, W.fpad, W.st->box[0], s));
                 PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
                             launch_drr_solver(W.fpad, W.fpad4, g, pd, V, y, W.pbuf, 1, 1, W.st, W.part_drr, s));
             }
@@ -604,7 +617,7 @@ int cost_grad_static(const float* f0, const float* mean, const float* U, int K, 
                      double* J, double* dJdw, double* ab, void* stream) {
     PCAS_TRY(check_vol(vol));
     if (!cb || cb->nu < 1 || cb->nv < 1) return fail(PCAS_ERR_INVALID_ARG, "detector size invalid");
-    const size_t need = layout(vol, cb).total;
+    const size_t need = layout(vol, cb, K < 1 ? 1 : K > PCAS_KMAX ? PCAS_KMAX : K).total;
     if (need > (size_t)PCAS_STATIC_SCRATCH_BYTES)
         return fail(PCAS_ERR_INVALID_ARG,
                     "cost_grad_static: this volume and detector need %zu bytes of scratch, more than the "

@@ -75,7 +75,15 @@ struct SolveState {
     int cur;                              // buffer holding P f(w)
     int phase, evals, trials;
     unsigned int counter[4];              // last-block counters (reset by the last block)
+    // Bounding box of the non-zero voxels of the warped volume (slot 0: f,
+    // slot 1: the union of the four candidates), as {xmin, ymin, zmin, -xmax,
+    // -ymax, -zmax} so that both ends reduce with atomicMin; "empty" is
+    // BOX_EMPTY everywhere.  Written by the warp kernels, read and reset by the
+    // projector that consumes the volume.
+    int box[2][6];
 };
+
+enum : int { BOX_EMPTY = 0x3fffffff };
 
 // Reduction scratch: per-block partials plus the counter used to find the
 // last block to finish (which then reduces all partials in a fixed order).
@@ -178,28 +186,35 @@ __device__ __forceinline__ float3 ray_dir(const View& V, int iu, int iv) {
 }
 
 // Range [i0, i1] of sample indices whose position Q0 + i step D lies in the
-// support box [-1, n_c]; empty when i0 > i1.  Rounding can add or drop a
-// sample right on the box surface, where the interpolant is zero.
-__device__ __forceinline__ void sample_range(const View& V, const Grid& g, float3 D, int& i0,
-                                             int& i1) {
+// box [lo_c, hi_c] (voxel units); empty when i0 > i1.  Rounding can add or
+// drop a sample right on the box surface, where the interpolant is zero.
+__device__ __forceinline__ void sample_range_box(const View& V, float3 D, const float lo[3],
+                                                 const float hi[3], int& i0, int& i1) {
     float tlo = -3.0e38f, thi = 3.0e38f;
     const float q0[3] = {V.Q0.x, V.Q0.y, V.Q0.z};
     const float d[3] = {D.x, D.y, D.z};
-    const float n[3] = {(float)g.nx, (float)g.ny, (float)g.nz};
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         if (d[c] != 0.0f) {
             float ia = 1.0f / d[c];
-            float t1 = (-1.0f - q0[c]) * ia, t2 = (n[c] - q0[c]) * ia;
+            float t1 = (lo[c] - q0[c]) * ia, t2 = (hi[c] - q0[c]) * ia;
             tlo = fmaxf(tlo, fminf(t1, t2));
             thi = fminf(thi, fmaxf(t1, t2));
-        } else if (q0[c] < -1.0f || q0[c] > n[c]) {
+        } else if (q0[c] < lo[c] || q0[c] > hi[c]) {
             tlo = 1.0f; thi = 0.0f;
         }
     }
-    if (tlo > thi) { i0 = 1; i1 = 0; return; }
+    if (!(tlo <= thi)) { i0 = 1; i1 = 0; return; }
     i0 = (int)ceilf(tlo / V.step);
     i1 = (int)floorf(thi / V.step);
+}
+
+// The support box [-1, n_c] of the zero-padded trilinear interpolant.
+__device__ __forceinline__ void sample_range(const View& V, const Grid& g, float3 D, int& i0,
+                                             int& i1) {
+    const float lo[3] = {-1.0f, -1.0f, -1.0f};
+    const float hi[3] = {(float)g.nx, (float)g.ny, (float)g.nz};
+    sample_range_box(V, D, lo, hi, i0, i1);
 }
 
 // --------------------------------------------------------------- reductions
@@ -284,7 +299,7 @@ cudaError_t launch_warp_dvf(const float* f0, const float* dvf, Grid g, float* f,
 // Solver warp: S = 1 writes f(w_src) to the scalar zero-halo buffer; S = 4
 // writes the four candidate volumes st->wt[0..3] interleaved (float4).
 cudaError_t launch_warp_pca(const float* f0, const float* mean, const float* U, int K, WSrc w,
-                            Grid g, Pad pd, float* fpad, cudaStream_t s);
+                            Grid g, Pad pd, float* fpad, int* box, cudaStream_t s);
 cudaError_t launch_warp_batch(const float* f0, const float* mean, const float* U, int K,
                               const SolveState* st, Grid g, Pad pd, float4* fpad4, cudaStream_t s);
 cudaError_t launch_drr_plain(const float* f, Grid g, const View& V, float* p, cudaStream_t s);
@@ -297,9 +312,19 @@ cudaError_t launch_resid(const float* pbuf, const float* y, const View& V, int f
                          SolveState* st, double* part, cudaStream_t s);
 cudaError_t launch_adjoint_plain(const float* img, Grid g, const View& V, float* gout,
                                  cudaStream_t s);
+// Scratch of the gradient pass: compacted voxels with a non-zero warp
+// Jacobian (index and h_k, per 8x8x4 tile) and the tile counts / offsets.
+struct AdjScratch {
+    int* act_idx;       // ntiles * 256
+    float* act_h;       // K * ntiles * 256
+    int* tile_count;    // ntiles
+    int* tile_off;      // ntiles + 1
+};
+inline long adj_tiles(int nx, int ny, int nz) { return (long)((nx + 7) / 8) * ((ny + 7) / 8) * ((nz + 3) / 4); }
 cudaError_t launch_adjoint_grad(const float4* rayt, Grid g, const View& V, const float* f0,
                                 const float* mean, const float* U, int K, int step_setup,
-                                SolveState* st, double* part, int max_blocks, cudaStream_t s);
+                                SolveState* st, double* part, const AdjScratch& as, int max_blocks,
+                                cudaStream_t s);
 cudaError_t launch_localize(const float* mean, const float* U, int K, const double* w, Grid g,
                             const double o[3], const double s_mm[3], const double c_ref[3],
                             int max_iter, double tol, double* out, cudaStream_t s);

@@ -34,6 +34,30 @@ __device__ __forceinline__ void dvf4(const float* __restrict__ mean, const float
     }
 }
 
+// Bounding box of the non-zero outputs of a block (thread-local boxes reduced
+// through warp shuffles, then one atomicMin per component and block): both
+// reductions are order-independent, so the box is deterministic.
+__device__ __forceinline__ void box_reduce(int b[6], int* __restrict__ out) {
+    __shared__ int s_b[kWarpThreads / 32][6];
+#pragma unroll
+    for (int t = 0; t < 6; t++)
+        for (int o = 16; o > 0; o >>= 1) b[t] = min(b[t], __shfl_xor_sync(0xffffffffu, b[t], o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int t = 0; t < 6; t++) s_b[wid][t] = b[t];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        int m = BOX_EMPTY;
+        for (int w = 0; w < kWarpThreads / 32; w++) m = min(m, s_b[w][threadIdx.x]);
+        if (m != BOX_EMPTY) atomicMin(out + threadIdx.x, m);
+    }
+}
+
+__device__ __forceinline__ void box_add(int b[6], int i, int j, int k) {
+    b[0] = min(b[0], i); b[1] = min(b[1], j); b[2] = min(b[2], k);
+    b[3] = min(b[3], -i); b[4] = min(b[4], -j); b[5] = min(b[5], -k);
+}
+
 // Eq. (1) alone: dvf = mean + U w.  One thread per 4 voxels (VEC) or 1 voxel.
 template <bool VEC>
 __global__ void __launch_bounds__(kWarpThreads)
@@ -79,30 +103,33 @@ template <bool VEC>
 __global__ void __launch_bounds__(kWarpThreads)
 k_warp_pca(const float* __restrict__ f0, const float* __restrict__ mean,
            const float* __restrict__ U, int K, WSrc ws, Grid g, Pad pd, long N,
-           float* __restrict__ fpad) {
+           float* __restrict__ fpad, int* __restrict__ box_out) {
     if (ws.phase && *ws.phase >= PH_STOP) return;
     __shared__ float s_w[PCAS_KMAX];
     if (threadIdx.x < PCAS_KMAX)
         s_w[threadIdx.x] = ws.dev ? (threadIdx.x < K ? (float)ws.dev[threadIdx.x] : 0.f)
                                   : ws.w[threadIdx.x];
     __syncthreads();
+    int b[6] = {BOX_EMPTY, BOX_EMPTY, BOX_EMPTY, BOX_EMPTY, BOX_EMPTY, BOX_EMPTY};
     long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (VEC) {
         long n = t * 4;
-        if (n >= N) return;
-        int i = (int)(n % g.nx);
-        long r = n / g.nx;
-        int j = (int)(r % g.ny), k = (int)(r / g.ny);
-        float x[3][4];
-        dvf4(mean, U, K, s_w, N, n, x);
-        float o[4];
+        if (n < N) {
+            int i = (int)(n % g.nx);
+            long r = n / g.nx;
+            int j = (int)(r % g.ny), k = (int)(r / g.ny);
+            float x[3][4];
+            dvf4(mean, U, K, s_w, N, n, x);
+            float o[4];
 #pragma unroll
-        for (int e = 0; e < 4; e++)
-            o[e] = tri_dense(f0, g, fmaf(x[0][e], g.inv_sx, (float)(i + e)),
-                             fmaf(x[1][e], g.inv_sy, (float)j), fmaf(x[2][e], g.inv_sz, (float)k));
-        *reinterpret_cast<float4*>(fpad + pad_index(pd, i, j, k)) = make_float4(o[0], o[1], o[2], o[3]);
-    } else {
-        if (t >= N) return;
+            for (int e = 0; e < 4; e++) {
+                o[e] = tri_dense(f0, g, fmaf(x[0][e], g.inv_sx, (float)(i + e)),
+                                 fmaf(x[1][e], g.inv_sy, (float)j), fmaf(x[2][e], g.inv_sz, (float)k));
+                if (o[e] != 0.0f) box_add(b, i + e, j, k);
+            }
+            *reinterpret_cast<float4*>(fpad + pad_index(pd, i, j, k)) = make_float4(o[0], o[1], o[2], o[3]);
+        }
+    } else if (t < N) {
         int i = (int)(t % g.nx);
         long r = t / g.nx;
         int j = (int)(r % g.ny), k = (int)(r / g.ny);
@@ -112,10 +139,12 @@ k_warp_pca(const float* __restrict__ f0, const float* __restrict__ mean,
             for (int kk = 0; kk < K; kk++) v = fmaf(s_w[kk], U[((long)kk * 3 + c) * N + t], v);
             x[c] = v;
         }
-        fpad[pad_index(pd, i, j, k)] =
-            tri_dense(f0, g, fmaf(x[0], g.inv_sx, (float)i), fmaf(x[1], g.inv_sy, (float)j),
-                      fmaf(x[2], g.inv_sz, (float)k));
+        const float o = tri_dense(f0, g, fmaf(x[0], g.inv_sx, (float)i), fmaf(x[1], g.inv_sy, (float)j),
+                                  fmaf(x[2], g.inv_sz, (float)k));
+        if (o != 0.0f) box_add(b, i, j, k);
+        fpad[pad_index(pd, i, j, k)] = o;
     }
+    box_reduce(b, box_out);
 }
 
 // Four candidate volumes of the line search at once (Eq. 1 + A.5 for each
@@ -126,7 +155,7 @@ k_warp_pca(const float* __restrict__ f0, const float* __restrict__ mean,
 __global__ void __launch_bounds__(kWarpThreads)
 k_warp_batch(const float* __restrict__ f0, const float* __restrict__ mean,
              const float* __restrict__ U, int K, const SolveState* st, Grid g, Pad pd, long N,
-             float4* __restrict__ fpad4) {
+             float4* __restrict__ fpad4, int* __restrict__ box_out) {
     if (st->phase >= PH_STOP) return;
     __shared__ float s_w[TRIAL_BATCH][PCAS_KMAX];
     if (threadIdx.x < TRIAL_BATCH * PCAS_KMAX) {
@@ -134,32 +163,36 @@ k_warp_batch(const float* __restrict__ f0, const float* __restrict__ mean,
         s_w[j][k] = k < K ? (float)st->wt[j][k] : 0.0f;
     }
     __syncthreads();
+    int bx[6] = {BOX_EMPTY, BOX_EMPTY, BOX_EMPTY, BOX_EMPTY, BOX_EMPTY, BOX_EMPTY};
     const long n = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
-    const int i = (int)(n % g.nx);
-    const long r = n / g.nx;
-    const int j = (int)(r % g.ny), k = (int)(r / g.ny);
-    float x[TRIAL_BATCH][3];
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-        const float m = mean ? __ldcs(mean + c * N + n) : 0.0f;
-#pragma unroll
-        for (int b = 0; b < TRIAL_BATCH; b++) x[b][c] = m;
-    }
-    for (int kk = 0; kk < K; kk++) {
+    if (n < N) {
+        const int i = (int)(n % g.nx);
+        const long r = n / g.nx;
+        const int j = (int)(r % g.ny), k = (int)(r / g.ny);
+        float x[TRIAL_BATCH][3];
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            const float u = __ldcs(U + ((long)kk * 3 + c) * N + n);
+            const float m = mean ? __ldcs(mean + c * N + n) : 0.0f;
 #pragma unroll
-            for (int b = 0; b < TRIAL_BATCH; b++) x[b][c] = fmaf(s_w[b][kk], u, x[b][c]);
+            for (int b = 0; b < TRIAL_BATCH; b++) x[b][c] = m;
         }
-    }
-    float o[TRIAL_BATCH];
+        for (int kk = 0; kk < K; kk++) {
 #pragma unroll
-    for (int b = 0; b < TRIAL_BATCH; b++)
-        o[b] = tri_dense(f0, g, fmaf(x[b][0], g.inv_sx, (float)i), fmaf(x[b][1], g.inv_sy, (float)j),
-                         fmaf(x[b][2], g.inv_sz, (float)k));
-    fpad4[pad_index(pd, i, j, k)] = make_float4(o[0], o[1], o[2], o[3]);
+            for (int c = 0; c < 3; c++) {
+                const float u = __ldcs(U + ((long)kk * 3 + c) * N + n);
+#pragma unroll
+                for (int b = 0; b < TRIAL_BATCH; b++) x[b][c] = fmaf(s_w[b][kk], u, x[b][c]);
+            }
+        }
+        float o[TRIAL_BATCH];
+#pragma unroll
+        for (int b = 0; b < TRIAL_BATCH; b++)
+            o[b] = tri_dense(f0, g, fmaf(x[b][0], g.inv_sx, (float)i), fmaf(x[b][1], g.inv_sy, (float)j),
+                             fmaf(x[b][2], g.inv_sz, (float)k));
+        fpad4[pad_index(pd, i, j, k)] = make_float4(o[0], o[1], o[2], o[3]);
+        if (o[0] != 0.0f || o[1] != 0.0f || o[2] != 0.0f || o[3] != 0.0f) box_add(bx, i, j, k);
+    }
+    box_reduce(bx, box_out);      // every thread of the block, one call site
 }
 
 inline bool aligned16(const void* p) { return p == nullptr || ((uintptr_t)p & 15u) == 0; }
@@ -186,18 +219,19 @@ cudaError_t launch_warp_dvf(const float* f0, const float* dvf, Grid g, float* f,
 }
 
 cudaError_t launch_warp_pca(const float* f0, const float* mean, const float* U, int K, WSrc w,
-                            Grid g, Pad pd, float* fpad, cudaStream_t s) {
+                            Grid g, Pad pd, float* fpad, int* box, cudaStream_t s) {
     long N = (long)g.nx * g.ny * g.nz;
     bool vec = (g.nx % 4 == 0) && aligned16(mean) && aligned16(U) && aligned16(fpad);
-    if (vec) k_warp_pca<true><<<blocks_for(N / 4), kWarpThreads, 0, s>>>(f0, mean, U, K, w, g, pd, N, fpad);
-    else k_warp_pca<false><<<blocks_for(N), kWarpThreads, 0, s>>>(f0, mean, U, K, w, g, pd, N, fpad);
+    if (vec) k_warp_pca<true><<<blocks_for(N / 4), kWarpThreads, 0, s>>>(f0, mean, U, K, w, g, pd, N, fpad, box);
+    else k_warp_pca<false><<<blocks_for(N), kWarpThreads, 0, s>>>(f0, mean, U, K, w, g, pd, N, fpad, box);
     return cudaGetLastError();
 }
 
 cudaError_t launch_warp_batch(const float* f0, const float* mean, const float* U, int K,
                               const SolveState* st, Grid g, Pad pd, float4* fpad4, cudaStream_t s) {
     long N = (long)g.nx * g.ny * g.nz;
-    k_warp_batch<<<blocks_for(N), kWarpThreads, 0, s>>>(f0, mean, U, K, st, g, pd, N, fpad4);
+    k_warp_batch<<<blocks_for(N), kWarpThreads, 0, s>>>(f0, mean, U, K, st, g, pd, N, fpad4,
+                                                         const_cast<int*>(st->box[1]));
     return cudaGetLastError();
 }
 

@@ -61,8 +61,9 @@ def test_workspace_bytes_host_only(lib):
     n = P.workspace_bytes(vol, cb, 3)
     npad = (((256 + 6) + 3) // 4 * 4) * 260 * 104          # two-voxel zero halo
     M = 512 * 384
-    need = npad * (4 + 16) + M * (5 * 4 + 32)               # f, 4 candidates, 5 projections, ray table
-    assert need <= n < need + 2_000_000 and n % 256 == 0
+    cap = 32 * 32 * 25 * 256                                 # 8x8x4 tiles of the Jacobian compaction
+    need = npad * (4 + 16) + M * (5 * 4 + 32) + cap * (4 + 4 * 3)   # f, 4 candidates, 5 projections,
+    assert need <= n < need + 2_000_000 and n % 256 == 0            # ray table, compacted voxels
     assert P.workspace_bytes(vol, cb, 0) == 0 and P.workspace_bytes(vol, cb, 9) == 0
 
 
