@@ -10,7 +10,8 @@ module only compiles it with gcc and marshals numpy arrays through ctypes.
 Parity status of each routine (what pins it is in ``tests/test_oracle_*.py``):
   pca_dvf, warp_volume, trilinear, trilinear_grad, drr_forward, drr_ray,
   drr_adjoint, intensity_fit, cost, cost_grad, grad_forward_mode,
-  solve_projection, localize_tumor, lp_fit, lp_predict -- all pinned.
+  warp_adjoint, cost_grad_f0, solve_projection, localize_tumor, lp_fit,
+  lp_predict -- all pinned.
 """
 from __future__ import annotations
 
@@ -88,6 +89,9 @@ def lib():
                                                C.c_double, C.c_int, _D, _D, _D]),
                 ("oracle_grad_forward_mode", C.c_int, [_D, _D, _D, C.c_int, _D, _D, C.POINTER(Vol),
                                                        C.POINTER(CB), C.c_double, C.c_double, C.c_double, _D]),
+                ("oracle_warp_adjoint", C.c_int, [_D, _D, C.POINTER(Vol), _D]),
+                ("oracle_cost_grad_f0", C.c_int, [_D, _D, _D, C.c_int, _D, _D, C.POINTER(Vol), C.POINTER(CB),
+                                                  C.c_double, C.c_int, _D, _D, _D]),
                 ("oracle_solve_projection", C.c_int, [_D, _D, _D, C.c_int, _D, C.POINTER(Vol), C.POINTER(CB),
                                                       _D, C.POINTER(Params), _D, C.POINTER(Stats), _D]),
                 ("oracle_localize_tumor", C.c_int, [_D, _D, C.c_int, _D, C.POINTER(Vol), _D, C.c_int,
@@ -212,6 +216,31 @@ def cost_grad(f0, mean, U, w, y, vol, cb, step, ab=None):
                                   C.byref(cb_struct(cb)), float(step), 1 if ab is None else 0,
                                   _p(abv), C.byref(J), _p(G)), "cost_grad")
     return J.value, G, (abv[0], abv[1])
+
+
+def warp_adjoint(z, dvf, vol):
+    z = _d(z).ravel()
+    dvf = _d(dvf).reshape(3, -1)
+    out = np.empty_like(z)
+    _check(lib().oracle_warp_adjoint(_p(z), _p(dvf), C.byref(vol_struct(vol)), _p(out)), "warp_adjoint")
+    return out
+
+
+def cost_grad_f0(f0, mean, U, w, y, vol, cb, step, ab=None):
+    """Returns (J, dJ/df0 (N,), (a, b)) at fixed w; (a, b) from Eq. (A.1) unless given."""
+    N = _nvox(vol)
+    f0 = _d(f0).ravel()
+    U = _d(U).reshape(-1, 3, N)
+    K = U.shape[0]
+    mean = None if mean is None else _d(mean).reshape(3, N)
+    w, y = _d(w), _d(y).ravel()
+    abv = np.zeros(2) if ab is None else _d(ab).copy()
+    J = C.c_double()
+    out = np.zeros(N)
+    _check(lib().oracle_cost_grad_f0(_p(f0), _p(mean), _p(U), K, _p(w), _p(y), C.byref(vol_struct(vol)),
+                                     C.byref(cb_struct(cb)), float(step), 1 if ab is None else 0, _p(abv),
+                                     C.byref(J), _p(out)), "cost_grad_f0")
+    return J.value, out, (abv[0], abv[1])
 
 
 def grad_forward_mode(f0, mean, U, w, y, vol, cb, step, a, b):

@@ -361,6 +361,57 @@ int oracle_grad_forward_mode(const double* f0, const double* mean, const double*
     return st;
 }
 
+
+/* ------------------------------------------------- warp transpose (W^T)
+ * The warp is linear in f0: f(v) = sum over the eight taps u of q(v) of
+ * weight(q(v), u) f0(u), with taps outside the grid dropped.  Its transpose
+ * scatters z(v) with the same weights. */
+int oracle_warp_adjoint(const double* z, const double* dvf, const ovol* vol, double* out) {
+    if (!vol_ok(vol) || !z || !dvf || !out) return 1;
+    long N = nvox(vol);
+    memset(out, 0, sizeof(double) * N);
+    for (long k = 0; k < vol->nz; k++)
+        for (long j = 0; j < vol->ny; j++)
+            for (long i = 0; i < vol->nx; i++) {
+                long n = (k * vol->ny + j) * vol->nx + i;
+                double q[3] = {i + dvf[n] / vol->sx, j + dvf[N + n] / vol->sy, k + dvf[2 * N + n] / vol->sz};
+                double fl[3] = {floor(q[0]), floor(q[1]), floor(q[2])};
+                double zz[3] = {q[0] - fl[0], q[1] - fl[1], q[2] - fl[2]};
+                for (int t = 0; t < 8; t++) {
+                    int a = t & 1, b = (t >> 1) & 1, cc = (t >> 2) & 1;
+                    long ii = (long)fl[0] + a, jj = (long)fl[1] + b, kk = (long)fl[2] + cc;
+                    if (ii < 0 || jj < 0 || kk < 0 || ii >= vol->nx || jj >= vol->ny || kk >= vol->nz)
+                        continue;
+                    double wgt = (a ? zz[0] : 1 - zz[0]) * (b ? zz[1] : 1 - zz[1]) * (cc ? zz[2] : 1 - zz[2]);
+                    out[(kk * vol->ny + jj) * vol->nx + ii] += wgt * z[n];
+                }
+            }
+    return 0;
+}
+
+int oracle_cost_grad_f0(const double* f0, const double* mean, const double* U, int K,
+                        const double* w, const double* y, const ovol* vol, const ocb* cb,
+                        double step, int fit_ab, double* ab, double* J, double* dJdf0) {
+    if (!vol_ok(vol) || !cb_ok(vol, cb, step) || K < 1 || !f0 || !U || !w || !y || !ab || !J || !dJdf0)
+        return 1;
+    long N = nvox(vol), M = (long)cb->nu * cb->nv;
+    double* dvf = malloc(sizeof(double) * 3 * N);
+    double* f = malloc(sizeof(double) * N);
+    double* g = malloc(sizeof(double) * N);
+    double* p = malloc(sizeof(double) * M);
+    double* r = malloc(sizeof(double) * M);
+    int st = render(f0, mean, U, K, w, vol, cb, step, dvf, f, p);
+    if (!st && fit_ab) st = oracle_intensity_fit(p, y, M, &ab[0], &ab[1]);
+    if (!st) {
+        *J = oracle_cost(p, y, M, ab[0], ab[1]);
+        for (long i = 0; i < M; i++) r[i] = 2.0 * (p[i] - ab[0] * y[i] - ab[1]);   /* dJ/dp */
+        st = oracle_drr_adjoint(r, vol, cb, step, g);                              /* dJ/df */
+    }
+    if (!st) st = oracle_warp_adjoint(g, dvf, vol, dJdf0);                         /* dJ/df0 */
+    free(dvf); free(f); free(g); free(p); free(r);
+    return st;
+}
+
 /* ------------------------------------------------- Appendix: the alternating solve
  * Each iteration: (A.1) refits (a, b) on the current projection; the gradient
  * at fixed (a, b) gives d = -G/||G||; Armijo backtracking from mu0 accepts the

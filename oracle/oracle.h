@@ -83,6 +83,16 @@ int oracle_cost_grad(const double* f0, const double* mean, const double* U, int 
 int oracle_grad_forward_mode(const double* f0, const double* mean, const double* U, int K,
                              const double* w, const double* y, const ovol* vol,
                              const ocb* cb, double step, double a, double b, double* G);
+/* Transpose of the warp of Eq. (A.5) for a fixed DVF: out[u] = sum_v z[v] *
+ * (trilinear weight of tap u at q(v)), i.e. <W x, z> = <x, W^T z>.  out
+ * overwritten (N doubles). */
+int oracle_warp_adjoint(const double* z, const double* dvf, const ovol* vol, double* out);
+/* Gradient of Eq. (2) with respect to the reference CT at fixed w and (a, b):
+ * dJ/df0 = W^T (2 P^T r), r = P W f0 - a y - b.  (a, b) from Eq. (A.1) at w
+ * when fit_ab != 0 (returned in ab).  Also returns J. */
+int oracle_cost_grad_f0(const double* f0, const double* mean, const double* U, int K,
+                        const double* w, const double* y, const ovol* vol, const ocb* cb,
+                        double step, int fit_ab, double* ab, double* J, double* dJdf0);
 /* Appendix: alternate (A.1) and (A.2) with Armijo backtracking.
  * J_trace (may be NULL) receives the cost after each iteration (max_iter+1). */
 int oracle_solve_projection(const double* f0, const double* mean, const double* U, int K,

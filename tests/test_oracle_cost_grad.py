@@ -91,3 +91,44 @@ def test_cost_grad_with_mean_field(problem):
     J2, G2, _ = O.cost_grad(P["f0"], None, P["U"], w + c, P["y_clean"], P["vol"], P["cb"], P["step"])
     assert abs(J1 - J2) <= 1e-9 * J2
     np.testing.assert_allclose(G1, G2, rtol=1e-8)
+
+
+# ------------------------------------------- gradient w.r.t. the reference CT
+def test_warp_adjoint_identity(problem):
+    """<W x, z> = <x, W^T z>: W^T is the exact transpose of the warp (A.5)."""
+    P = problem
+    dvf = O.pca_dvf(None, P["U"], np.array([0.7, -0.4, 0.5]), P["vol"])
+    g = S.rng(12)
+    x = g.uniform(0, 1, dvf.shape[1])
+    z = g.uniform(0, 1, dvf.shape[1])
+    lhs = O.warp_volume(x, dvf, P["vol"]) @ z
+    rhs = x @ O.warp_adjoint(z, dvf, P["vol"])
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_grad_f0_exact_central_differences(problem):
+    """At fixed w and (a, b), J is exactly quadratic in f0 (P and W are linear),
+    so a central difference along any direction equals the directional
+    derivative up to rounding."""
+    P = problem
+    w = np.array([0.3, -0.1, 0.05])
+    y = P["y_clean"] + S.gaussian_noise(P["y_clean"].shape, 0.01 * P["y_clean"].max(), 13, np.float64)
+    J, dJ, ab = O.cost_grad_f0(P["f0"], None, P["U"], w, y, P["vol"], P["cb"], P["step"])
+    J2, _, _ = O.cost_grad(P["f0"], None, P["U"], w, y, P["vol"], P["cb"], P["step"])
+    assert abs(J - J2) <= 1e-12 * J
+    g = S.rng(14)
+    f0 = P["f0"].astype(np.float64)
+    for _ in range(3):
+        dirn = g.standard_normal(f0.shape)
+        h = 1e-3
+        Jp = O.cost_grad_f0(f0 + h * dirn, None, P["U"], w, y, P["vol"], P["cb"], P["step"], ab=ab)[0]
+        Jm = O.cost_grad_f0(f0 - h * dirn, None, P["U"], w, y, P["vol"], P["cb"], P["step"], ab=ab)[0]
+        fd = (Jp - Jm) / (2 * h)
+        assert abs(fd - dJ @ dirn.ravel()) <= 1e-9 * max(abs(fd), 1e-12)
+    # single voxels too (the per-voxel check of the differentiation workload)
+    flat = f0.ravel()
+    for n in g.integers(0, flat.size, 8):
+        e = np.zeros_like(flat); e[n] = 1e-2
+        Jp = O.cost_grad_f0(flat + e, None, P["U"], w, y, P["vol"], P["cb"], P["step"], ab=ab)[0]
+        Jm = O.cost_grad_f0(flat - e, None, P["U"], w, y, P["vol"], P["cb"], P["step"], ab=ab)[0]
+        assert abs((Jp - Jm) / 2e-2 - dJ[n]) <= 1e-9 * max(abs(dJ).max(), 1e-12)
