@@ -117,6 +117,22 @@ int cost_grad(const float* f0, const float* mean, const float* U, int K, const d
               const float* y, const pcas_vol* vol, const pcas_cb* cb, double step_mm,
               double* J, double* dJdw, double* ab, void* ws, size_t ws_bytes, void* stream);
 
+/* Differentiation of Eq. (2) with respect to w and the reference CT.
+ * J*(w, f0) = min over (a, b) of J is evaluated with (a, b) from Eq. (A.1);
+ * since (a, b) minimise J, the gradients of J* are the partial derivatives at
+ * that (a, b): dJ/dw as in cost_grad, and dJ/df0 = W^T (2 P^T r) with W the
+ * trilinear warp of Eq. (A.5) at x(w) (the chain rule below Eq. A.2 stopped at
+ * f instead of x).  The warped volume is recomputed on every call, never kept.
+ * dJdw (K, host) may be NULL: then only J and (a, b) are computed.  dJdf0
+ * (N floats, device) may be NULL; if given, dJdw must be given too.  The
+ * scatter of W^T accumulates in 64-bit fixed point (deterministic).
+ * Workspace: pcas_workspace_bytes_f0 (device, 256-byte aligned).  Synchronous. */
+size_t pcas_workspace_bytes_f0(const pcas_vol* vol, const pcas_cb* cb, int K);
+int cost_grad_f0(const float* f0, const float* mean, const float* U, int K, const double* w,
+                 const float* y, const pcas_vol* vol, const pcas_cb* cb, double step_mm,
+                 double* J, double* dJdw, double* ab, float* dJdf0, void* ws, size_t ws_bytes,
+                 void* stream);
+
 /* cost_grad without a caller workspace: the paper has no counterpart.  For
  * callers that cannot allocate device memory -- code recorded into a CUDA
  * graph by stream capture, real-time loops where an allocation could stall,
@@ -194,7 +210,8 @@ enum {
     PCAS_K_INIT = 9,         /* solver state reset                              */
     PCAS_K_WARP_BATCH = 10,  /* four line-search candidates warped at once      */
     PCAS_K_DRR_BATCH = 11,   /* four candidates projected and tested at once    */
-    PCAS_K_COUNT = 12
+    PCAS_K_GRAD_F0 = 12,     /* dJ/df0: full backprojection + warp transpose    */
+    PCAS_K_COUNT = 13
 };
 int pcas_profile(int on);
 int pcas_profile_read(int kind, long long* launches, double* total_ms);

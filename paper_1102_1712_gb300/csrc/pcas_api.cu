@@ -481,6 +481,67 @@ int cost_grad(const float* f0, const float* mean, const float* U, int K, const d
     return PCAS_OK;
 }
 
+size_t pcas_workspace_bytes_f0(const pcas_vol* vol, const pcas_cb* cb, int K) {
+    if (check_vol(vol) != PCAS_OK || !cb || cb->nu < 1 || cb->nv < 1 || K < 1 || K > PCAS_KMAX) return 0;
+    const size_t N = (size_t)vol->nx * vol->ny * vol->nz;
+    return layout(vol, cb, K).total + align256(N * sizeof(float)) + align256(N * 8) + 256;
+}
+
+int cost_grad_f0(const float* f0, const float* mean, const float* U, int K, const double* w,
+                 const float* y, const pcas_vol* vol, const pcas_cb* cb, double step_mm, double* J,
+                 double* dJdw, double* ab, float* dJdf0, void* ws, size_t ws_bytes, void* stream) {
+    PCAS_TRY(check_vol(vol));
+    PCAS_TRY(check_model(mean, U, K));
+    PCAS_TRY(check_ptr(f0, "f0"));
+    PCAS_TRY(check_ptr(y, "y"));
+    PCAS_TRY(check_ptr(w, "w"));
+    PCAS_TRY(check_ptr(J, "J"));
+    PCAS_TRY(check_ptr(ab, "ab"));
+    PCAS_TRY(check_finite(w, K, "w"));
+    if (dJdf0 && !dJdw) return fail(PCAS_ERR_INVALID_ARG, "dJdf0 needs dJdw (the gradient passes run together)");
+    View V;
+    PCAS_TRY(make_view(vol, cb, step_mm, &V));
+    if (!ws) return fail(PCAS_ERR_INVALID_ARG, "workspace is NULL");
+    const size_t need = pcas_workspace_bytes_f0(vol, cb, K);
+    if (ws_bytes < need) return fail(PCAS_ERR_INVALID_ARG, "workspace too small: %zu < %zu bytes", ws_bytes, need);
+    Ws W;
+    const size_t base = layout(vol, cb, K).total;
+    PCAS_TRY(bind_ws(ws, base, vol, cb, K, &W));
+    const size_t N = (size_t)vol->nx * vol->ny * vol->nz;
+    char* extra = static_cast<char*>(ws) + base;
+    float* z = reinterpret_cast<float*>(extra);
+    unsigned long long* acc = reinterpret_cast<unsigned long long*>(extra + align256(N * sizeof(float)));
+    unsigned int* zmax = reinterpret_cast<unsigned int*>(extra + align256(N * sizeof(float)) + align256(N * 8));
+    cudaStream_t s = as_stream(stream);
+    Grid g = make_grid(vol);
+    Pad pd = make_pad(vol->nx, vol->ny, vol->nz);
+    PCAS_CUDA(cudaMemsetAsync(W.fpad, 0, W.fpad_bytes, s));
+    PCAS_TRY(launch_init(W.st, K, w, nullptr, s));
+    WSrc wsrc{};
+    wsrc.dev = W.st->w;
+    wsrc.phase = &W.st->phase;
+    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, K, wsrc, g, pd, W.fpad, W.st->box[0], s));
+    PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
+                launch_drr_solver(W.fpad, W.fpad4, g, pd, V, y, W.pbuf, 0, 1, W.st, W.part_drr, s));
+    PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, 1, W.rayt, W.st, W.part_res, s));
+    if (dJdw)
+        PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
+                    launch_adjoint_grad(W.rayt, g, V, f0, mean, U, K, 0, W.st, W.part_adj, W.adj,
+                                        adjoint_block_cap(), s));
+    if (dJdf0)
+        PCAS_LAUNCH(PCAS_K_GRAD_F0, s, launch_grad_f0(W.rayt, g, V, mean, U, K, W.st, z, zmax, acc, dJdf0, s));
+    SolveState h;
+    PCAS_CUDA(cudaMemcpyAsync(&h, W.st, sizeof(h), cudaMemcpyDeviceToHost, s));
+    PCAS_CUDA(cudaStreamSynchronize(s));
+    if (h.phase == PH_SINGULAR) return fail(PCAS_ERR_SINGULAR, "Y^T Y is singular (constant image y)");
+    *J = h.J;
+    if (dJdw)
+        for (int k = 0; k < K; k++) dJdw[k] = h.G[k];
+    ab[0] = h.a;
+    ab[1] = h.b;
+    return PCAS_OK;
+}
+
 int solve_projection(const float* f0, const float* mean, const float* U, int K, const float* y,
                      const pcas_vol* vol, const pcas_cb* cb, const double* w_init,
                      const pcas_params* prm, double* w_out, pcas_stats* stats, void* ws,

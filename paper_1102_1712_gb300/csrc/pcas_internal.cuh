@@ -325,6 +325,11 @@ cudaError_t launch_adjoint_grad(const float4* rayt, Grid g, const View& V, const
                                 const float* mean, const float* U, int K, int step_setup,
                                 SolveState* st, double* part, const AdjScratch& as, int max_blocks,
                                 cudaStream_t s);
+// dJ/df0 = W^T (2 P^T r): z (N floats) and acc (N 64-bit) are scratch,
+// zmax_bits one word; out (N floats) receives the gradient.
+cudaError_t launch_grad_f0(const float4* rayt, Grid g, const View& V, const float* mean, const float* U,
+                           int K, const SolveState* st, float* z, unsigned int* zmax_bits,
+                           unsigned long long* acc, float* out, cudaStream_t s);
 cudaError_t launch_localize(const float* mean, const float* U, int K, const double* w, Grid g,
                             const double o[3], const double s_mm[3], const double c_ref[3],
                             int max_iter, double tol, double* out, cudaStream_t s);

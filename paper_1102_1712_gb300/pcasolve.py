@@ -68,6 +68,9 @@ _SIGS = {
     "drr_adjoint": (C.c_int, [_P, C.POINTER(Vol), C.POINTER(CB), C.c_double, _P, _P]),
     "cost_grad": (C.c_int, [_P, _P, _P, C.c_int, _D, _P, C.POINTER(Vol), C.POINTER(CB), C.c_double,
                             _D, _D, _D, _P, C.c_size_t, _P]),
+    "pcas_workspace_bytes_f0": (C.c_size_t, [C.POINTER(Vol), C.POINTER(CB), C.c_int]),
+    "cost_grad_f0": (C.c_int, [_P, _P, _P, C.c_int, _D, _P, C.POINTER(Vol), C.POINTER(CB), C.c_double,
+                               _D, _D, _D, _P, _P, C.c_size_t, _P]),
     "cost_grad_static": (C.c_int, [_P, _P, _P, C.c_int, _D, _P, C.POINTER(Vol), C.POINTER(CB),
                                    C.c_double, _D, _D, _D, _P]),
     "solve_projection": (C.c_int, [_P, _P, _P, C.c_int, _P, C.POINTER(Vol), C.POINTER(CB), _D,
@@ -81,7 +84,7 @@ _SIGS = {
 
 # kernel classes of pcas_profile_read (include/pcasolve.h)
 KERNELS = ["warp_pca", "drr_solver", "resid", "adjoint_grad", "drr_forward", "drr_adjoint",
-           "pca_dvf", "warp_volume", "localize", "init", "warp_batch", "drr_batch"]
+           "pca_dvf", "warp_volume", "localize", "init", "warp_batch", "drr_batch", "grad_f0"]
 
 
 def lib():
@@ -250,6 +253,42 @@ def cost_grad(f0, mean, U, w, y, vol, cb, step, ws: Workspace = None, stream=Non
                            C.byref(g), float(step), C.byref(J), G.ctypes.data_as(_D),
                            ab.ctypes.data_as(_D), ws.ptr, ws.nbytes, _stream(stream)))
     return J.value, G, (ab[0], ab[1])
+
+
+class WorkspaceF0(Workspace):
+    """Device workspace for cost_grad_f0."""
+
+    def __init__(self, vol, cb, K, device=None):
+        import torch
+        n = int(lib().pcas_workspace_bytes_f0(C.byref(vol_struct(vol)), C.byref(cb_struct(cb)), int(K)))
+        if n == 0:
+            raise ValueError("invalid volume / view / K for a workspace")
+        self.buf = torch.empty(n + 256, dtype=torch.uint8, device=device or "cuda")
+        self.ptr = (self.buf.data_ptr() + 255) & ~255
+        self.nbytes = n
+
+
+def cost_grad_f0(f0, mean, U, w, y, vol, cb, step, want_grad=True, want_grad_f0=True,
+                 ws: Workspace = None, out=None, stream=None):
+    """Returns (J, dJ/dw (K,) or None, (a, b), dJ/df0 (N,) device tensor or None)."""
+    import torch
+    N = _nvox(vol)
+    K = _K(U, vol)
+    g = cb_struct(cb)
+    ws = ws or WorkspaceF0(vol, cb, K, device=U.device)
+    wv = _host_d(w, K)
+    J = C.c_double()
+    G = np.zeros(K) if (want_grad or want_grad_f0) else None
+    ab = np.zeros(2)
+    if want_grad_f0 and out is None:
+        out = torch.empty(N, dtype=torch.float32, device=U.device)
+    _check(lib().cost_grad_f0(_dev(f0, "f0", N), _dev(mean, "mean", 3 * N), _dev(U, "U"), K,
+                              wv.ctypes.data_as(_D), _dev(y, "y", g.nu * g.nv), C.byref(vol_struct(vol)),
+                              C.byref(g), float(step), C.byref(J),
+                              None if G is None else G.ctypes.data_as(_D), ab.ctypes.data_as(_D),
+                              _dev(out, "dJdf0", N) if want_grad_f0 else None, ws.ptr, ws.nbytes,
+                              _stream(stream)))
+    return J.value, G, (ab[0], ab[1]), (out if want_grad_f0 else None)
 
 
 def cost_grad_static(f0, mean, U, w, y, vol, cb, step, stream=None):
