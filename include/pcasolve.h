@@ -180,6 +180,27 @@ int localize_tumor(const float* mean, const float* U, int K, const double* w,
                    const pcas_vol* vol, const double c_ref[3], int max_iter, double tol_mm,
                    double c_out[3], void* stream);
 
+/* ------------------------------------------------------------------------
+ * Storage precision of the reference CT and the motion model.  The *_typed
+ * calls take f0, mean and U as float (PCAS_F32), bfloat16 (PCAS_BF16) or half
+ * (PCAS_F16) arrays with the layouts above; every value is widened to float
+ * on load, so interpolation, DVF synthesis, projection and accumulation stay
+ * float32, and the cross-block reductions and scalar updates FP64 (Appendix
+ * arithmetic unchanged).  The plain calls are the PCAS_F32 case.  Halves the
+ * model and CT traffic of the warp and Jacobian passes. */
+typedef enum { PCAS_F32 = 0, PCAS_BF16 = 1, PCAS_F16 = 2 } pcas_dtype;
+int cost_grad_typed(const void* f0, const void* mean, const void* U, int dtype, int K,
+                    const double* w, const float* y, const pcas_vol* vol, const pcas_cb* cb,
+                    double step_mm, double* J, double* dJdw, double* ab, void* ws, size_t ws_bytes,
+                    void* stream);
+int solve_projection_typed(const void* f0, const void* mean, const void* U, int dtype, int K,
+                           const float* y, const pcas_vol* vol, const pcas_cb* cb,
+                           const double* w_init, const pcas_params* params, double* w_out,
+                           pcas_stats* stats, void* ws, size_t ws_bytes, void* stream);
+int localize_tumor_typed(const void* mean, const void* U, int dtype, int K, const double* w,
+                         const pcas_vol* vol, const double c_ref[3], int max_iter, double tol_mm,
+                         double c_out[3], void* stream);
+
 /* Eq. (3): per coefficient k, least-squares fit over t = L..T-1 of
  * trace[t][k] ~ sum_{l=1..L} c[k][l-1] trace[t-l][k].  trace: host T x K;
  * c: host K x L.  Needs T > 2L.  Host only. */

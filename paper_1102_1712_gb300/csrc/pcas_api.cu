@@ -143,7 +143,7 @@ int make_view(const pcas_vol* vol, const pcas_cb* cb, double step, View* V) {
     return PCAS_OK;
 }
 
-int check_model(const float* mean, const float* U, int K) {
+int check_model(const void* mean, const void* U, int K) {
     (void)mean;
     if (K < 1 || K > PCAS_KMAX) return fail(PCAS_ERR_INVALID_ARG, "K must be in [1, %d], got %d", PCAS_KMAX, K);
     if (!U) return fail(PCAS_ERR_INVALID_ARG, "U is NULL");
@@ -222,7 +222,8 @@ int adjoint_block_cap() {
 }
 
 // ------------------------------------------------------------ small kernels
-__global__ void k_localize(const float* __restrict__ mean, const float* __restrict__ U, int K,
+template <typename T>
+__global__ void k_localize(const T* __restrict__ mean, const T* __restrict__ U, int K,
                            Grid g, double w0, double w1, double w2, double w3, double w4, double w5,
                            double w6, double w7, double ox, double oy, double oz, double isx,
                            double isy, double isz, double cx, double cy, double cz, int max_iter,
@@ -254,8 +255,8 @@ __global__ void k_localize(const float* __restrict__ mean, const float* __restri
             if (inside && wt != 0.0) {
                 long v = (idx[2] * g.ny + idx[1]) * g.nx + idx[0];
                 for (int c = 0; c < 3; c++) {
-                    double val = mean ? (double)mean[c * N + v] : 0.0;
-                    for (int k = 0; k < K; k++) val += w[k] * (double)U[((long)k * 3 + c) * N + v];
+                    double val = mean ? (double)ldg_f(mean + c * N + v) : 0.0;
+                    for (int k = 0; k < K; k++) val += w[k] * (double)ldg_f(U + ((long)k * 3 + c) * N + v);
                     x[c] = wt * val;
                 }
             }
@@ -315,6 +316,12 @@ int launch_init(SolveState* st, int K, const double* w, const pcas_params* prm, 
     return PCAS_OK;
 }
 
+int check_dtype(int dt) {
+    if (dt != PCAS_F32 && dt != PCAS_BF16 && dt != PCAS_F16)
+        return fail(PCAS_ERR_INVALID_ARG, "storage dtype must be PCAS_F32, PCAS_BF16 or PCAS_F16, got %d", dt);
+    return PCAS_OK;
+}
+
 int check_ptr(const void* p, const char* name) {
     if (!p) return fail(PCAS_ERR_INVALID_ARG, "%s is NULL", name);
     return PCAS_OK;
@@ -334,18 +341,18 @@ int check_finite(const double* v, int n, const char* name) {
 
 // Everything up to and including the gradient at st->w: warp, DRR with
 // moments, (A.1) + residual + J, fused adjoint gradient.
-int eval_gradient_pipeline(const float* f0, const float* mean, const float* U, int K, const float* y,
+int eval_gradient_pipeline(const void* f0, const void* mean, const void* U, int dt, int K, const float* y,
                            const Grid& g, const Pad& pd, const View& V, const Ws& W, int step_setup,
                            cudaStream_t s) {
     WSrc ws{};
     ws.dev = W.st->w;
     ws.phase = &W.st->phase;
-    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, K, ws, g, pd, W.fpad, W.st->box[0], s));
+    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, dt, K, ws, g, pd, W.fpad, W.st->box[0], s));
     PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
                 launch_drr_solver(W.fpad, W.fpad4, g, pd, V, y, W.pbuf, 0, 1, W.st, W.part_drr, s));
     PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, 1, W.rayt, W.st, W.part_res, s));
     PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
-                launch_adjoint_grad(W.rayt, g, V, f0, mean, U, K, step_setup, W.st, W.part_adj, W.adj,
+                launch_adjoint_grad(W.rayt, g, V, f0, mean, U, dt, K, step_setup, W.st, W.part_adj, W.adj,
                                     adjoint_block_cap(), s));
     return PCAS_OK;
 }
@@ -410,7 +417,7 @@ int pca_dvf(const float* mean, const float* U, int K, const double* w, const pca
     float wf[PCAS_KMAX] = {0};
     for (int k = 0; k < K; k++) wf[k] = (float)w[k];
     cudaStream_t s = as_stream(stream);
-    PCAS_LAUNCH(PCAS_K_PCA_DVF, s, launch_pca_dvf(mean, U, K, wf, make_grid(vol), dvf, s));
+    PCAS_LAUNCH(PCAS_K_PCA_DVF, s, launch_pca_dvf(mean, U, DT_F32, K, wf, make_grid(vol), dvf, s));
     return PCAS_OK;
 }
 
@@ -420,7 +427,7 @@ int warp_volume(const float* f0, const float* dvf, const pcas_vol* vol, float* f
     PCAS_TRY(check_ptr(dvf, "dvf"));
     PCAS_TRY(check_ptr(f, "f"));
     cudaStream_t s = as_stream(stream);
-    PCAS_LAUNCH(PCAS_K_WARP_DVF, s, launch_warp_dvf(f0, dvf, make_grid(vol), f, s));
+    PCAS_LAUNCH(PCAS_K_WARP_DVF, s, launch_warp_dvf(f0, DT_F32, dvf, make_grid(vol), f, s));
     return PCAS_OK;
 }
 
@@ -448,11 +455,12 @@ int drr_adjoint(const float* img, const pcas_vol* vol, const pcas_cb* cb, double
     return PCAS_OK;
 }
 
-int cost_grad(const float* f0, const float* mean, const float* U, int K, const double* w,
-              const float* y, const pcas_vol* vol, const pcas_cb* cb, double step_mm, double* J,
-              double* dJdw, double* ab, void* ws, size_t ws_bytes, void* stream) {
+int cost_grad_typed(const void* f0, const void* mean, const void* U, int dtype, int K, const double* w,
+                    const float* y, const pcas_vol* vol, const pcas_cb* cb, double step_mm, double* J,
+                    double* dJdw, double* ab, void* ws, size_t ws_bytes, void* stream) {
     PCAS_TRY(check_vol(vol));
     PCAS_TRY(check_model(mean, U, K));
+    PCAS_TRY(check_dtype(dtype));
     PCAS_TRY(check_ptr(f0, "f0"));
     PCAS_TRY(check_ptr(y, "y"));
     PCAS_TRY(check_ptr(w, "w"));
@@ -469,7 +477,7 @@ int cost_grad(const float* f0, const float* mean, const float* U, int K, const d
     Pad pd = make_pad(vol->nx, vol->ny, vol->nz);
     PCAS_CUDA(cudaMemsetAsync(W.fpad, 0, W.fpad_bytes, s));
     PCAS_TRY(launch_init(W.st, K, w, nullptr, s));
-    PCAS_TRY(eval_gradient_pipeline(f0, mean, U, K, y, g, pd, V, W, 0, s));
+    PCAS_TRY(eval_gradient_pipeline(f0, mean, U, dtype, K, y, g, pd, V, W, 0, s));
     SolveState h;
     PCAS_CUDA(cudaMemcpyAsync(&h, W.st, sizeof(h), cudaMemcpyDeviceToHost, s));
     PCAS_CUDA(cudaStreamSynchronize(s));
@@ -479,6 +487,12 @@ int cost_grad(const float* f0, const float* mean, const float* U, int K, const d
     ab[0] = h.a;
     ab[1] = h.b;
     return PCAS_OK;
+}
+
+int cost_grad(const float* f0, const float* mean, const float* U, int K, const double* w,
+              const float* y, const pcas_vol* vol, const pcas_cb* cb, double step_mm, double* J,
+              double* dJdw, double* ab, void* ws, size_t ws_bytes, void* stream) {
+    return cost_grad_typed(f0, mean, U, PCAS_F32, K, w, y, vol, cb, step_mm, J, dJdw, ab, ws, ws_bytes, stream);
 }
 
 size_t pcas_workspace_bytes_f0(const pcas_vol* vol, const pcas_cb* cb, int K) {
@@ -520,13 +534,13 @@ int cost_grad_f0(const float* f0, const float* mean, const float* U, int K, cons
     WSrc wsrc{};
     wsrc.dev = W.st->w;
     wsrc.phase = &W.st->phase;
-    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, K, wsrc, g, pd, W.fpad, W.st->box[0], s));
+    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, DT_F32, K, wsrc, g, pd, W.fpad, W.st->box[0], s));
     PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
                 launch_drr_solver(W.fpad, W.fpad4, g, pd, V, y, W.pbuf, 0, 1, W.st, W.part_drr, s));
     PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, 1, W.rayt, W.st, W.part_res, s));
     if (dJdw)
         PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
-                    launch_adjoint_grad(W.rayt, g, V, f0, mean, U, K, 0, W.st, W.part_adj, W.adj,
+                    launch_adjoint_grad(W.rayt, g, V, f0, mean, U, DT_F32, K, 0, W.st, W.part_adj, W.adj,
                                         adjoint_block_cap(), s));
     if (dJdf0)
         PCAS_LAUNCH(PCAS_K_GRAD_F0, s, launch_grad_f0(W.rayt, g, V, mean, U, K, W.st, z, zmax, acc, dJdf0, s));
@@ -542,12 +556,13 @@ int cost_grad_f0(const float* f0, const float* mean, const float* U, int K, cons
     return PCAS_OK;
 }
 
-int solve_projection(const float* f0, const float* mean, const float* U, int K, const float* y,
-                     const pcas_vol* vol, const pcas_cb* cb, const double* w_init,
-                     const pcas_params* prm, double* w_out, pcas_stats* stats, void* ws,
-                     size_t ws_bytes, void* stream) {
+int solve_projection_typed(const void* f0, const void* mean, const void* U, int dtype, int K,
+                           const float* y, const pcas_vol* vol, const pcas_cb* cb, const double* w_init,
+                           const pcas_params* prm, double* w_out, pcas_stats* stats, void* ws,
+                           size_t ws_bytes, void* stream) {
     PCAS_TRY(check_vol(vol));
     PCAS_TRY(check_model(mean, U, K));
+    PCAS_TRY(check_dtype(dtype));
     PCAS_TRY(check_ptr(f0, "f0"));
     PCAS_TRY(check_ptr(y, "y"));
     PCAS_TRY(check_ptr(w_init, "w_init"));
@@ -572,14 +587,14 @@ int solve_projection(const float* f0, const float* mean, const float* U, int K, 
     wcur.phase = &W.st->phase;
     wtrial.dev = W.st->wt[0];
     wtrial.phase = &W.st->phase;
-    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, K, wcur, g, pd, W.fpad, W.st->box[0], s));
+    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, dtype, K, wcur, g, pd, W.fpad, W.st->box[0], s));
     PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
                 launch_drr_solver(W.fpad, W.fpad4, g, pd, V, y, W.pbuf, 0, 1, W.st, W.part_drr, s));
     int iters = 0, phase = PH_RUNNING;
     for (int it = 0; it < prm->max_iter; it++) {
         PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, it == 0, W.rayt, W.st, W.part_res, s));
         PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
-                    launch_adjoint_grad(W.rayt, g, V, f0, mean, U, K, 1, W.st, W.part_adj, W.adj, adj_cap, s));
+                    launch_adjoint_grad(W.rayt, g, V, f0, mean, U, dtype, K, 1, W.st, W.part_adj, W.adj, adj_cap, s));
         // Armijo backtracking over the schedule mu0, beta mu0, ...: the next (up
         // to four) step sizes that the rule may still try are rendered and
         // tested in one pass; the device accepts the first that passes, in
@@ -602,12 +617,12 @@ int solve_projection(const float* f0, const float* mean, const float* U, int K, 
                 break;
             }
             if (nvalid >= 2) {
-                PCAS_LAUNCH(PCAS_K_WARP_BATCH, s, launch_warp_batch(f0, mean, U, K, W.st, g, pd, W.fpad4, s));
+                PCAS_LAUNCH(PCAS_K_WARP_BATCH, s, launch_warp_batch(f0, mean, U, dtype, K, W.st, g, pd, W.fpad4, s));
                 PCAS_LAUNCH(PCAS_K_DRR_BATCH, s,
                             launch_drr_solver(W.fpad, W.fpad4, g, pd, V, y, W.pbuf, TRIAL_BATCH, nvalid,
                                               W.st, W.part_drr, s));
             } else {
-                PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, K, wtrial, g, pd, W.fpad, W.st->box[0], s));
+                PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, dtype, K, wtrial, g, pd, W.fpad, W.st->box[0], s));
                 PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
                             launch_drr_solver(W.fpad, W.fpad4, g, pd, V, y, W.pbuf, 1, 1, W.st, W.part_drr, s));
             }
@@ -636,6 +651,14 @@ int solve_projection(const float* f0, const float* mean, const float* U, int K, 
         stats->mu_last = h.mu;
     }
     return PCAS_OK;
+}
+
+int solve_projection(const float* f0, const float* mean, const float* U, int K, const float* y,
+                     const pcas_vol* vol, const pcas_cb* cb, const double* w_init,
+                     const pcas_params* prm, double* w_out, pcas_stats* stats, void* ws,
+                     size_t ws_bytes, void* stream) {
+    return solve_projection_typed(f0, mean, U, PCAS_F32, K, y, vol, cb, w_init, prm, w_out, stats, ws,
+                                  ws_bytes, stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -690,11 +713,12 @@ int cost_grad_static(const float* f0, const float* mean, const float* U, int K, 
                      (size_t)PCAS_STATIC_SCRATCH_BYTES, stream);
 }
 
-int localize_tumor(const float* mean, const float* U, int K, const double* w, const pcas_vol* vol,
-                   const double c_ref[3], int max_iter, double tol_mm, double c_out[3],
-                   void* stream) {
+int localize_tumor_typed(const void* mean, const void* U, int dtype, int K, const double* w,
+                         const pcas_vol* vol, const double c_ref[3], int max_iter, double tol_mm,
+                         double c_out[3], void* stream) {
     PCAS_TRY(check_vol(vol));
     PCAS_TRY(check_model(mean, U, K));
+    PCAS_TRY(check_dtype(dtype));
     PCAS_TRY(check_ptr(w, "w"));
     PCAS_TRY(check_ptr(c_ref, "c_ref"));
     PCAS_TRY(check_ptr(c_out, "c_out"));
@@ -710,17 +734,29 @@ int localize_tumor(const float* mean, const float* U, int K, const double* w, co
     std::lock_guard<std::mutex> lock(g_localize_mutex);
     double* out = nullptr;
     PCAS_CUDA(cudaGetSymbolAddress((void**)&out, d_localize_out));
-    PCAS_LAUNCH(PCAS_K_LOCALIZE, s,
-                (k_localize<<<1, 32, 0, s>>>(mean, U, K, make_grid(vol), wv[0], wv[1], wv[2], wv[3],
-                                             wv[4], wv[5], wv[6], wv[7], vol->ox, vol->oy, vol->oz,
-                                             1.0 / vol->sx, 1.0 / vol->sy, 1.0 / vol->sz, c_ref[0],
-                                             c_ref[1], c_ref[2], max_iter, tol_mm, out),
-                 cudaGetLastError()));
+#define PCAS_LOC(T)                                                                                  \
+    PCAS_LAUNCH(PCAS_K_LOCALIZE, s,                                                                  \
+                (k_localize<T><<<1, 32, 0, s>>>(static_cast<const T*>(mean), static_cast<const T*>(U), \
+                                                K, make_grid(vol), wv[0], wv[1], wv[2], wv[3], wv[4],  \
+                                                wv[5], wv[6], wv[7], vol->ox, vol->oy, vol->oz,        \
+                                                1.0 / vol->sx, 1.0 / vol->sy, 1.0 / vol->sz, c_ref[0], \
+                                                c_ref[1], c_ref[2], max_iter, tol_mm, out),            \
+                 cudaGetLastError()))
+    if (dtype == PCAS_F32) PCAS_LOC(float);
+    else if (dtype == PCAS_BF16) PCAS_LOC(__nv_bfloat16);
+    else PCAS_LOC(__half);
+#undef PCAS_LOC
     double h[4];
     PCAS_CUDA(cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, s));
     PCAS_CUDA(cudaStreamSynchronize(s));
     c_out[0] = h[0]; c_out[1] = h[1]; c_out[2] = h[2];
     return h[3] != 0.0 ? PCAS_OK : PCAS_NOT_CONVERGED;
+}
+
+int localize_tumor(const float* mean, const float* U, int K, const double* w, const pcas_vol* vol,
+                   const double c_ref[3], int max_iter, double tol_mm, double c_out[3],
+                   void* stream) {
+    return localize_tumor_typed(mean, U, PCAS_F32, K, w, vol, c_ref, max_iter, tol_mm, c_out, stream);
 }
 
 // Eq. (3) fit, host: per coefficient, normal equations of the order-L

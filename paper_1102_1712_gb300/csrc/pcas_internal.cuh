@@ -2,6 +2,8 @@
 // translation units of libpcasolve (sm_103a).  Not part of the C ABI.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -92,11 +94,47 @@ struct Reduce {
     unsigned int* counter;
 };
 
+// ------------------------------------------------------ storage types
+// The reference CT and the motion model may be stored as float, bfloat16 or
+// half; every value is widened to float on load (interpolation, DVF synthesis
+// and accumulation are float).
+template <typename T> __device__ __forceinline__ float ldg_f(const T* p);
+template <> __device__ __forceinline__ float ldg_f<float>(const float* p) { return __ldg(p); }
+template <> __device__ __forceinline__ float ldg_f<__nv_bfloat16>(const __nv_bfloat16* p) {
+    return __bfloat162float(__ldg(p));
+}
+template <> __device__ __forceinline__ float ldg_f<__half>(const __half* p) { return __half2float(__ldg(p)); }
+
+// Four consecutive values, streaming (evict-first); p 16-byte (float) or
+// 8-byte (16-bit types) aligned.
+template <typename T> __device__ __forceinline__ float4 ld4_stream(const T* p);
+template <> __device__ __forceinline__ float4 ld4_stream<float>(const float* p) {
+    return __ldcs(reinterpret_cast<const float4*>(p));
+}
+template <> __device__ __forceinline__ float4 ld4_stream<__nv_bfloat16>(const __nv_bfloat16* p) {
+    const uint2 u = __ldcs(reinterpret_cast<const uint2*>(p));
+    return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                       __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+}
+template <> __device__ __forceinline__ float4 ld4_stream<__half>(const __half* p) {
+    const uint2 u = __ldcs(reinterpret_cast<const uint2*>(p));
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+template <typename T> __device__ __forceinline__ float ldcs_f(const T* p);
+template <> __device__ __forceinline__ float ldcs_f<float>(const float* p) { return __ldcs(p); }
+template <> __device__ __forceinline__ float ldcs_f<__nv_bfloat16>(const __nv_bfloat16* p) {
+    return __bfloat162float(__ldcs(p));
+}
+template <> __device__ __forceinline__ float ldcs_f<__half>(const __half* p) { return __half2float(__ldcs(p)); }
+
 // ------------------------------------------------------------- trilinear
 // Eq. (A.5): trilinear interpolation with zero outside the grid, on the dense
 // [nz][ny][nx] layout.  Positions are clamped to [-2, n+1] first so that
 // conversion to int is always defined (values there are zero anyway).
-__device__ __forceinline__ float tri_dense(const float* __restrict__ f, const Grid& g,
+template <typename T>
+__device__ __forceinline__ float tri_dense(const T* __restrict__ f, const Grid& g,
                                            float qx, float qy, float qz) {
     qx = fminf(fmaxf(qx, -2.0f), (float)g.nx + 1.0f);
     qy = fminf(fmaxf(qy, -2.0f), (float)g.ny + 1.0f);
@@ -107,17 +145,17 @@ __device__ __forceinline__ float tri_dense(const float* __restrict__ f, const Gr
     const long sy = g.nx, sz = (long)g.nx * g.ny;
     float v000, v100, v010, v110, v001, v101, v011, v111;
     if (lx >= 0 && ly >= 0 && lz >= 0 && lx < g.nx - 1 && ly < g.ny - 1 && lz < g.nz - 1) {
-        const float* b = f + lz * sz + ly * sy + lx;
-        v000 = __ldg(b);          v100 = __ldg(b + 1);
-        v010 = __ldg(b + sy);     v110 = __ldg(b + sy + 1);
-        v001 = __ldg(b + sz);     v101 = __ldg(b + sz + 1);
-        v011 = __ldg(b + sz + sy); v111 = __ldg(b + sz + sy + 1);
+        const T* b = f + lz * sz + ly * sy + lx;
+        v000 = ldg_f(b);           v100 = ldg_f(b + 1);
+        v010 = ldg_f(b + sy);      v110 = ldg_f(b + sy + 1);
+        v001 = ldg_f(b + sz);      v101 = ldg_f(b + sz + 1);
+        v011 = ldg_f(b + sz + sy); v111 = ldg_f(b + sz + sy + 1);
     } else {
         const bool x0 = lx >= 0 && lx < g.nx, x1 = lx + 1 >= 0 && lx + 1 < g.nx;
         const bool y0 = ly >= 0 && ly < g.ny, y1 = ly + 1 >= 0 && ly + 1 < g.ny;
         const bool z0 = lz >= 0 && lz < g.nz, z1 = lz + 1 >= 0 && lz + 1 < g.nz;
         auto at = [&](bool ok, int i, int j, int k) -> float {
-            return ok ? __ldg(f + k * sz + j * sy + i) : 0.0f;
+            return ok ? ldg_f(f + k * sz + j * sy + i) : 0.0f;
         };
         v000 = at(x0 && y0 && z0, lx, ly, lz);
         v100 = at(x1 && y0 && z0, lx + 1, ly, lz);
@@ -293,14 +331,17 @@ struct WSrc {                 // where a PCA-model kernel takes w from
     const int* phase;         // early exit when *phase >= PH_STOP (may be null)
 };
 
-cudaError_t launch_pca_dvf(const float* mean, const float* U, int K, const float* w, Grid g,
+// Storage type of f0 / mean / U (values of pcas_dtype in pcasolve.h).
+enum DType : int { DT_F32 = 0, DT_BF16 = 1, DT_F16 = 2 };
+
+cudaError_t launch_pca_dvf(const void* mean, const void* U, int dt, int K, const float* w, Grid g,
                            float* dvf, cudaStream_t s);
-cudaError_t launch_warp_dvf(const float* f0, const float* dvf, Grid g, float* f, cudaStream_t s);
+cudaError_t launch_warp_dvf(const void* f0, int dt, const float* dvf, Grid g, float* f, cudaStream_t s);
 // Solver warp: S = 1 writes f(w_src) to the scalar zero-halo buffer; S = 4
 // writes the four candidate volumes st->wt[0..3] interleaved (float4).
-cudaError_t launch_warp_pca(const float* f0, const float* mean, const float* U, int K, WSrc w,
+cudaError_t launch_warp_pca(const void* f0, const void* mean, const void* U, int dt, int K, WSrc w,
                             Grid g, Pad pd, float* fpad, int* box, cudaStream_t s);
-cudaError_t launch_warp_batch(const float* f0, const float* mean, const float* U, int K,
+cudaError_t launch_warp_batch(const void* f0, const void* mean, const void* U, int dt, int K,
                               const SolveState* st, Grid g, Pad pd, float4* fpad4, cudaStream_t s);
 cudaError_t launch_drr_plain(const float* f, Grid g, const View& V, float* p, cudaStream_t s);
 // Solver projector.  mode 0: first evaluation into buffer cur; mode 1: one
@@ -321,8 +362,8 @@ struct AdjScratch {
     int* tile_off;      // ntiles + 1
 };
 inline long adj_tiles(int nx, int ny, int nz) { return (long)((nx + 7) / 8) * ((ny + 7) / 8) * ((nz + 3) / 4); }
-cudaError_t launch_adjoint_grad(const float4* rayt, Grid g, const View& V, const float* f0,
-                                const float* mean, const float* U, int K, int step_setup,
+cudaError_t launch_adjoint_grad(const float4* rayt, Grid g, const View& V, const void* f0,
+                                const void* mean, const void* U, int dt, int K, int step_setup,
                                 SolveState* st, double* part, const AdjScratch& as, int max_blocks,
                                 cudaStream_t s);
 // dJ/df0 = W^T (2 P^T r): z (N floats) and acc (N 64-bit) are scratch,

@@ -9,12 +9,9 @@ namespace {
 
 constexpr int kWarpThreads = 256;
 
-__device__ __forceinline__ float4 ld4_stream(const float* p) {
-    return __ldcs(reinterpret_cast<const float4*>(p));
-}
-
 // Eq. (1) on four consecutive voxels: x_c = mean_c + sum_k w_k U_kc.
-__device__ __forceinline__ void dvf4(const float* __restrict__ mean, const float* __restrict__ U,
+template <typename T>
+__device__ __forceinline__ void dvf4(const T* __restrict__ mean, const T* __restrict__ U,
                                      int K, const float* w, long N, long n, float x[3][4]) {
 #pragma unroll
     for (int c = 0; c < 3; c++) {
@@ -59,9 +56,9 @@ __device__ __forceinline__ void box_add(int b[6], int i, int j, int k) {
 }
 
 // Eq. (1) alone: dvf = mean + U w.  One thread per 4 voxels (VEC) or 1 voxel.
-template <bool VEC>
+template <bool VEC, typename T>
 __global__ void __launch_bounds__(kWarpThreads)
-k_pca_dvf(const float* __restrict__ mean, const float* __restrict__ U, int K, WSrc ws, long N,
+k_pca_dvf(const T* __restrict__ mean, const T* __restrict__ U, int K, WSrc ws, long N,
           float* __restrict__ dvf) {
     long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (VEC) {
@@ -75,16 +72,17 @@ k_pca_dvf(const float* __restrict__ mean, const float* __restrict__ U, int K, WS
     } else {
         if (t >= N) return;
         for (int c = 0; c < 3; c++) {
-            float x = mean ? mean[c * N + t] : 0.0f;
-            for (int k = 0; k < K; k++) x = fmaf(ws.w[k], U[((long)k * 3 + c) * N + t], x);
+            float x = mean ? ldg_f(mean + c * N + t) : 0.0f;
+            for (int k = 0; k < K; k++) x = fmaf(ws.w[k], ldg_f(U + ((long)k * 3 + c) * N + t), x);
             dvf[c * N + t] = x;
         }
     }
 }
 
 // Warp by an explicit DVF (public warp_volume): one voxel per thread, dense out.
+template <typename T>
 __global__ void __launch_bounds__(kWarpThreads)
-k_warp_dvf(const float* __restrict__ f0, const float* __restrict__ dvf, Grid g, long N,
+k_warp_dvf(const T* __restrict__ f0, const float* __restrict__ dvf, Grid g, long N,
            float* __restrict__ f) {
     long n = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
@@ -99,10 +97,10 @@ k_warp_dvf(const float* __restrict__ f0, const float* __restrict__ dvf, Grid g, 
 
 // Fused DVF synthesis + warp into the zero-halo layout used by the solver.
 // VEC: 4 voxels per thread along x (nx % 4 == 0, 16-byte aligned model).
-template <bool VEC>
+template <bool VEC, typename T>
 __global__ void __launch_bounds__(kWarpThreads)
-k_warp_pca(const float* __restrict__ f0, const float* __restrict__ mean,
-           const float* __restrict__ U, int K, WSrc ws, Grid g, Pad pd, long N,
+k_warp_pca(const T* __restrict__ f0, const T* __restrict__ mean,
+           const T* __restrict__ U, int K, WSrc ws, Grid g, Pad pd, long N,
            float* __restrict__ fpad, int* __restrict__ box_out) {
     if (ws.phase && *ws.phase >= PH_STOP) return;
     __shared__ float s_w[PCAS_KMAX];
@@ -135,8 +133,8 @@ k_warp_pca(const float* __restrict__ f0, const float* __restrict__ mean,
         int j = (int)(r % g.ny), k = (int)(r / g.ny);
         float x[3];
         for (int c = 0; c < 3; c++) {
-            float v = mean ? mean[c * N + t] : 0.0f;
-            for (int kk = 0; kk < K; kk++) v = fmaf(s_w[kk], U[((long)kk * 3 + c) * N + t], v);
+            float v = mean ? ldg_f(mean + c * N + t) : 0.0f;
+            for (int kk = 0; kk < K; kk++) v = fmaf(s_w[kk], ldg_f(U + ((long)kk * 3 + c) * N + t), v);
             x[c] = v;
         }
         const float o = tri_dense(f0, g, fmaf(x[0], g.inv_sx, (float)i), fmaf(x[1], g.inv_sy, (float)j),
@@ -152,9 +150,10 @@ k_warp_pca(const float* __restrict__ f0, const float* __restrict__ mean,
 // coefficient vectors; each DVF is formed in the same operation order as the
 // single-volume warp, so a candidate's volume is bit-identical to a lone
 // evaluation.  Output: one float4 (f_0..f_3) per voxel, zero-halo layout.
+template <typename T>
 __global__ void __launch_bounds__(kWarpThreads)
-k_warp_batch(const float* __restrict__ f0, const float* __restrict__ mean,
-             const float* __restrict__ U, int K, const SolveState* st, Grid g, Pad pd, long N,
+k_warp_batch(const T* __restrict__ f0, const T* __restrict__ mean,
+             const T* __restrict__ U, int K, const SolveState* st, Grid g, Pad pd, long N,
              float4* __restrict__ fpad4, int* __restrict__ box_out) {
     if (st->phase >= PH_STOP) return;
     __shared__ float s_w[TRIAL_BATCH][PCAS_KMAX];
@@ -172,14 +171,14 @@ k_warp_batch(const float* __restrict__ f0, const float* __restrict__ mean,
         float x[TRIAL_BATCH][3];
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            const float m = mean ? __ldcs(mean + c * N + n) : 0.0f;
+            const float m = mean ? ldcs_f(mean + c * N + n) : 0.0f;
 #pragma unroll
             for (int b = 0; b < TRIAL_BATCH; b++) x[b][c] = m;
         }
         for (int kk = 0; kk < K; kk++) {
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                const float u = __ldcs(U + ((long)kk * 3 + c) * N + n);
+                const float u = ldcs_f(U + ((long)kk * 3 + c) * N + n);
 #pragma unroll
                 for (int b = 0; b < TRIAL_BATCH; b++) x[b][c] = fmaf(s_w[b][kk], u, x[b][c]);
             }
@@ -195,44 +194,76 @@ k_warp_batch(const float* __restrict__ f0, const float* __restrict__ mean,
     box_reduce(bx, box_out);      // every thread of the block, one call site
 }
 
-inline bool aligned16(const void* p) { return p == nullptr || ((uintptr_t)p & 15u) == 0; }
+inline bool aligned(const void* p, unsigned a) { return p == nullptr || ((uintptr_t)p & (a - 1)) == 0; }
 
 inline unsigned blocks_for(long work) { return (unsigned)((work + kWarpThreads - 1) / kWarpThreads); }
 
-}  // namespace
-
-cudaError_t launch_pca_dvf(const float* mean, const float* U, int K, const float* w, Grid g,
-                           float* dvf, cudaStream_t s) {
+template <typename T>
+cudaError_t pca_dvf_t(const void* mean, const void* U, int K, const float* w, Grid g, float* dvf,
+                      cudaStream_t s) {
     long N = (long)g.nx * g.ny * g.nz;
     WSrc ws{};
     for (int k = 0; k < K && k < PCAS_KMAX; k++) ws.w[k] = w[k];
-    bool vec = (N % 4 == 0) && aligned16(mean) && aligned16(U) && aligned16(dvf);
-    if (vec) k_pca_dvf<true><<<blocks_for(N / 4), kWarpThreads, 0, s>>>(mean, U, K, ws, N, dvf);
-    else k_pca_dvf<false><<<blocks_for(N), kWarpThreads, 0, s>>>(mean, U, K, ws, N, dvf);
+    const unsigned a = sizeof(T) * 4;
+    bool vec = (N % 4 == 0) && aligned(mean, a) && aligned(U, a) && aligned(dvf, 16);
+    const T* m = static_cast<const T*>(mean);
+    const T* u = static_cast<const T*>(U);
+    if (vec) k_pca_dvf<true, T><<<blocks_for(N / 4), kWarpThreads, 0, s>>>(m, u, K, ws, N, dvf);
+    else k_pca_dvf<false, T><<<blocks_for(N), kWarpThreads, 0, s>>>(m, u, K, ws, N, dvf);
     return cudaGetLastError();
 }
 
-cudaError_t launch_warp_dvf(const float* f0, const float* dvf, Grid g, float* f, cudaStream_t s) {
+template <typename T>
+cudaError_t warp_pca_t(const void* f0, const void* mean, const void* U, int K, WSrc w, Grid g, Pad pd,
+                       float* fpad, int* box, cudaStream_t s) {
     long N = (long)g.nx * g.ny * g.nz;
-    k_warp_dvf<<<blocks_for(N), kWarpThreads, 0, s>>>(f0, dvf, g, N, f);
+    const unsigned a = sizeof(T) * 4;
+    bool vec = (g.nx % 4 == 0) && aligned(mean, a) && aligned(U, a) && aligned(fpad, 16);
+    const T* f = static_cast<const T*>(f0);
+    const T* m = static_cast<const T*>(mean);
+    const T* u = static_cast<const T*>(U);
+    if (vec) k_warp_pca<true, T><<<blocks_for(N / 4), kWarpThreads, 0, s>>>(f, m, u, K, w, g, pd, N, fpad, box);
+    else k_warp_pca<false, T><<<blocks_for(N), kWarpThreads, 0, s>>>(f, m, u, K, w, g, pd, N, fpad, box);
     return cudaGetLastError();
 }
 
-cudaError_t launch_warp_pca(const float* f0, const float* mean, const float* U, int K, WSrc w,
+}  // namespace
+
+#define PCAS_DT_DISPATCH(dt, CALL)                                         \
+    switch (dt) {                                                          \
+        case DT_F32: { using T = float; return CALL; }                     \
+        case DT_BF16: { using T = __nv_bfloat16; return CALL; }            \
+        case DT_F16: { using T = __half; return CALL; }                    \
+        default: return cudaErrorInvalidValue;                             \
+    }
+
+cudaError_t launch_pca_dvf(const void* mean, const void* U, int dt, int K, const float* w, Grid g,
+                           float* dvf, cudaStream_t s) {
+    PCAS_DT_DISPATCH(dt, (pca_dvf_t<T>(mean, U, K, w, g, dvf, s)))
+}
+
+cudaError_t launch_warp_dvf(const void* f0, int dt, const float* dvf, Grid g, float* f, cudaStream_t s) {
+    long N = (long)g.nx * g.ny * g.nz;
+    PCAS_DT_DISPATCH(dt, (k_warp_dvf<T><<<blocks_for(N), kWarpThreads, 0, s>>>(static_cast<const T*>(f0), dvf, g,
+                                                                              N, f),
+                          cudaGetLastError()))
+}
+
+cudaError_t launch_warp_pca(const void* f0, const void* mean, const void* U, int dt, int K, WSrc w,
                             Grid g, Pad pd, float* fpad, int* box, cudaStream_t s) {
-    long N = (long)g.nx * g.ny * g.nz;
-    bool vec = (g.nx % 4 == 0) && aligned16(mean) && aligned16(U) && aligned16(fpad);
-    if (vec) k_warp_pca<true><<<blocks_for(N / 4), kWarpThreads, 0, s>>>(f0, mean, U, K, w, g, pd, N, fpad, box);
-    else k_warp_pca<false><<<blocks_for(N), kWarpThreads, 0, s>>>(f0, mean, U, K, w, g, pd, N, fpad, box);
-    return cudaGetLastError();
+    PCAS_DT_DISPATCH(dt, (warp_pca_t<T>(f0, mean, U, K, w, g, pd, fpad, box, s)))
 }
 
-cudaError_t launch_warp_batch(const float* f0, const float* mean, const float* U, int K,
+cudaError_t launch_warp_batch(const void* f0, const void* mean, const void* U, int dt, int K,
                               const SolveState* st, Grid g, Pad pd, float4* fpad4, cudaStream_t s) {
     long N = (long)g.nx * g.ny * g.nz;
-    k_warp_batch<<<blocks_for(N), kWarpThreads, 0, s>>>(f0, mean, U, K, st, g, pd, N, fpad4,
-                                                         const_cast<int*>(st->box[1]));
-    return cudaGetLastError();
+    int* box = const_cast<int*>(st->box[1]);
+    PCAS_DT_DISPATCH(dt, (k_warp_batch<T><<<blocks_for(N), kWarpThreads, 0, s>>>(
+                              static_cast<const T*>(f0), static_cast<const T*>(mean),
+                              static_cast<const T*>(U), K, st, g, pd, N, fpad4, box),
+                          cudaGetLastError()))
 }
+
+#undef PCAS_DT_DISPATCH
 
 }  // namespace pcas

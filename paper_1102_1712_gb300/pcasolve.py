@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libpcasolve.so")
 KMAX = 8
 
 OK, INVALID_ARG, SINGULAR, CUDA_ERROR, NOT_CONVERGED, TIMEOUT = range(6)
+F32, BF16, F16 = range(3)      # storage types of the *_typed calls (pcas_dtype)
 
 
 class PcasError(RuntimeError):
@@ -71,6 +72,12 @@ _SIGS = {
     "pcas_workspace_bytes_f0": (C.c_size_t, [C.POINTER(Vol), C.POINTER(CB), C.c_int]),
     "cost_grad_f0": (C.c_int, [_P, _P, _P, C.c_int, _D, _P, C.POINTER(Vol), C.POINTER(CB), C.c_double,
                                _D, _D, _D, _P, _P, C.c_size_t, _P]),
+    "cost_grad_typed": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, _D, _P, C.POINTER(Vol), C.POINTER(CB),
+                                  C.c_double, _D, _D, _D, _P, C.c_size_t, _P]),
+    "solve_projection_typed": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, _P, C.POINTER(Vol), C.POINTER(CB), _D,
+                                         C.POINTER(Params), _D, C.POINTER(Stats), _P, C.c_size_t, _P]),
+    "localize_tumor_typed": (C.c_int, [_P, _P, C.c_int, C.c_int, _D, C.POINTER(Vol), _D, C.c_int,
+                                       C.c_double, _D, _P]),
     "cost_grad_static": (C.c_int, [_P, _P, _P, C.c_int, _D, _P, C.POINTER(Vol), C.POINTER(CB),
                                    C.c_double, _D, _D, _D, _P]),
     "solve_projection": (C.c_int, [_P, _P, _P, C.c_int, _P, C.POINTER(Vol), C.POINTER(CB), _D,
@@ -136,15 +143,17 @@ def params_struct(p) -> Params:
                   int(p["max_trials"]), p["step"])
 
 
-def _dev(t, name, numel=None):
-    """Device pointer of a contiguous float32 CUDA tensor (None -> NULL)."""
+def _dev(t, name, numel=None, dtype=None):
+    """Device pointer of a contiguous CUDA tensor (None -> NULL); float32 unless
+    ``dtype`` (a torch dtype) says otherwise."""
     if t is None:
         return None
     import torch
+    dtype = dtype or torch.float32
     if not (isinstance(t, torch.Tensor) and t.is_cuda):
         raise TypeError(f"{name} must be a CUDA tensor")
-    if t.dtype != torch.float32 or not t.is_contiguous():
-        raise TypeError(f"{name} must be contiguous float32")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be contiguous {dtype}")
     if numel is not None and t.numel() != numel:
         raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
     return t.data_ptr()
@@ -238,8 +247,15 @@ def drr_adjoint(img, vol, cb, step, out=None, stream=None):
     return out
 
 
+def storage_type(U):
+    """pcas_dtype of the motion model tensor (float32, bfloat16 or float16)."""
+    import torch
+    return {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}[U.dtype]
+
+
 def cost_grad(f0, mean, U, w, y, vol, cb, step, ws: Workspace = None, stream=None):
-    """Returns (J, dJ/dw (K,), (a, b)) at w."""
+    """Returns (J, dJ/dw (K,), (a, b)) at w.  f0, mean and U share one storage
+    type (float32, bfloat16 or float16; float32 arithmetic either way)."""
     N = _nvox(vol)
     K = _K(U, vol)
     g = cb_struct(cb)
@@ -248,10 +264,12 @@ def cost_grad(f0, mean, U, w, y, vol, cb, step, ws: Workspace = None, stream=Non
     J = C.c_double()
     G = np.zeros(K)
     ab = np.zeros(2)
-    _check(lib().cost_grad(_dev(f0, "f0", N), _dev(mean, "mean", 3 * N), _dev(U, "U"), K,
-                           wv.ctypes.data_as(_D), _dev(y, "y", g.nu * g.nv), C.byref(vol_struct(vol)),
-                           C.byref(g), float(step), C.byref(J), G.ctypes.data_as(_D),
-                           ab.ctypes.data_as(_D), ws.ptr, ws.nbytes, _stream(stream)))
+    dt = U.dtype
+    _check(lib().cost_grad_typed(_dev(f0, "f0", N, dt), _dev(mean, "mean", 3 * N, dt), _dev(U, "U", None, dt),
+                                 storage_type(U), K, wv.ctypes.data_as(_D), _dev(y, "y", g.nu * g.nv),
+                                 C.byref(vol_struct(vol)), C.byref(g), float(step), C.byref(J),
+                                 G.ctypes.data_as(_D), ab.ctypes.data_as(_D), ws.ptr, ws.nbytes,
+                                 _stream(stream)))
     return J.value, G, (ab[0], ab[1])
 
 
@@ -320,10 +338,12 @@ def solve_projection(f0, mean, U, y, vol, cb, w_init, params, ws: Workspace = No
     w_out = np.zeros(K)
     st = Stats()
     prm = params_struct(params)
-    _check(lib().solve_projection(_dev(f0, "f0", N), _dev(mean, "mean", 3 * N), _dev(U, "U"), K,
-                                  _dev(y, "y", g.nu * g.nv), C.byref(vol_struct(vol)), C.byref(g),
-                                  w0.ctypes.data_as(_D), C.byref(prm), w_out.ctypes.data_as(_D),
-                                  C.byref(st), ws.ptr, ws.nbytes, _stream(stream)))
+    dt = U.dtype
+    _check(lib().solve_projection_typed(_dev(f0, "f0", N, dt), _dev(mean, "mean", 3 * N, dt),
+                                        _dev(U, "U", None, dt), storage_type(U), K,
+                                        _dev(y, "y", g.nu * g.nv), C.byref(vol_struct(vol)), C.byref(g),
+                                        w0.ctypes.data_as(_D), C.byref(prm), w_out.ctypes.data_as(_D),
+                                        C.byref(st), ws.ptr, ws.nbytes, _stream(stream)))
     return w_out, {k: getattr(st, k) for k, _ in Stats._fields_}
 
 
@@ -334,9 +354,10 @@ def localize_tumor(mean, U, w, vol, c_ref, max_iter=50, tol_mm=1e-6, stream=None
     wv = _host_d(w, K)
     cr = _host_d(c_ref, 3)
     out = np.zeros(3)
-    rc = lib().localize_tumor(_dev(mean, "mean", 3 * N), _dev(U, "U"), K, wv.ctypes.data_as(_D),
-                              C.byref(vol_struct(vol)), cr.ctypes.data_as(_D), int(max_iter),
-                              float(tol_mm), out.ctypes.data_as(_D), _stream(stream))
+    dt = U.dtype
+    rc = lib().localize_tumor_typed(_dev(mean, "mean", 3 * N, dt), _dev(U, "U", None, dt), storage_type(U), K,
+                                    wv.ctypes.data_as(_D), C.byref(vol_struct(vol)), cr.ctypes.data_as(_D),
+                                    int(max_iter), float(tol_mm), out.ctypes.data_as(_D), _stream(stream))
     _check(rc, allow=(OK, NOT_CONVERGED))
     return out, rc == OK
 

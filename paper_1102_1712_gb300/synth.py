@@ -97,16 +97,45 @@ def _smooth(a: np.ndarray, sig_vox) -> np.ndarray:
     return gaussian_filter(a, sigma=sig_vox, mode="constant", cval=0.0, truncate=3.0)
 
 
+def _upsample_linear(a: np.ndarray, shape) -> np.ndarray:
+    """Separable linear interpolation of a coarse grid onto ``shape`` (end points aligned)."""
+    out = a.astype(np.float32)
+    for ax, n in enumerate(shape):
+        m = out.shape[ax]
+        if m == n:
+            continue
+        x = np.linspace(0.0, m - 1.0, n, dtype=np.float64)
+        i0 = np.minimum(np.floor(x).astype(np.int64), m - 2)
+        t = (x - i0).astype(np.float32)
+        sh = [1] * out.ndim
+        sh[ax] = n
+        t = t.reshape(sh)
+        out = np.take(out, i0, axis=ax) * (1 - t) + np.take(out, i0 + 1, axis=ax) * t
+    return out
+
+
 def eigen_dvfs(vol: dict, K: int, seed: int, sigma_mm: float = 8.0, peak_mm: float = 10.0,
-               dtype=np.float32) -> np.ndarray:
-    """K smoothed random vector fields, shape [K, 3, nz*ny*nx], in mm."""
+               dtype=np.float32, coarse=(1, 1, 1)) -> np.ndarray:
+    """K smoothed random vector fields, shape [K, 3, nz*ny*nx], in mm.
+
+    ``coarse`` = (cz, cy, cx) > 1 draws the white noise on a grid that much
+    coarser, smooths it there (same sigma in mm) and interpolates linearly to
+    the full grid: for large volumes, where smoothing at full resolution would
+    take minutes.  The fields stay smooth at the sigma scale."""
     g = rng(seed)
     shape = (vol["nz"], vol["ny"], vol["nx"])
-    sig = (sigma_mm / vol["sz"], sigma_mm / vol["sy"], sigma_mm / vol["sx"])
+    cz, cy, cx = coarse
+    cshape = (-(-shape[0] // cz), -(-shape[1] // cy), -(-shape[2] // cx))
+    sig = (sigma_mm / (vol["sz"] * cz), sigma_mm / (vol["sy"] * cy), sigma_mm / (vol["sx"] * cx))
     N = int(np.prod(shape))
     U = np.empty((K, 3, N), dtype)
+
+    def field():
+        f = _smooth(g.standard_normal(cshape), sig)
+        return f if cshape == shape else _upsample_linear(f, shape)
+
     for k in range(K):
-        comps = [_smooth(g.standard_normal(shape), sig) for _ in range(3)]
+        comps = [field() for _ in range(3)]
         peaks = [np.abs(c).max() for c in comps]
         ref = peaks[2] if k == 0 else max(peaks)
         for c in range(3):
@@ -125,8 +154,12 @@ def translation_dvfs(vol: dict, K: int = 3, mm: float = 10.0, dtype=np.float32) 
 
 def breathing_trace(n: int, fps: float, period_s: float = 4.0, amp_mm: float = 15.0,
                     K: int = 3, irregular: bool = False, drift_mm: float = 0.0,
-                    jitter: float = 0.3, seed: int = 0, t0: float = 0.0) -> np.ndarray:
-    """Planted coefficients w(t), shape [n, K], sampled at ``fps``."""
+                    jitter: float = 0.3, seed: int = 0, t0: float = 0.0,
+                    amp_jitter: float | None = None) -> np.ndarray:
+    """Planted coefficients w(t), shape [n, K], sampled at ``fps``.  Irregular
+    traces scale each cycle's period by 1 + U(-jitter, jitter) and its
+    amplitude by 1 + U(-amp_jitter, amp_jitter) (amp_jitter defaults to jitter)."""
+    amp_jitter = jitter if amp_jitter is None else amp_jitter
     g = rng(seed)
     t = t0 + np.arange(n) / fps
     tmax = t[-1] + 2 * period_s
@@ -134,7 +167,7 @@ def breathing_trace(n: int, fps: float, period_s: float = 4.0, amp_mm: float = 1
     starts, periods, amps = [t0 - period_s], [], []
     while starts[-1] < tmax:
         pf = 1.0 + (g.uniform(-jitter, jitter) if irregular else 0.0)
-        af = 1.0 + (g.uniform(-jitter, jitter) if irregular else 0.0)
+        af = 1.0 + (g.uniform(-amp_jitter, amp_jitter) if irregular else 0.0)
         periods.append(period_s * pf)
         amps.append(amp_mm * af)
         starts.append(starts[-1] + periods[-1])
