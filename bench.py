@@ -33,6 +33,15 @@ WORKLOAD = dict(name="sequence-256x256x100-K3-512x384", vol=(256, 256, 100, 2.0,
                 tumor_mm=20.0, seeds=dict(phantom=10, dvf=11, noise=12), noise=0.01)
 METRIC = "projections/s solved (warp+DRR+adjoint iters), % HBM roofline, mm error"
 
+# Precision workload (not the default bench line): 512x512x160 CT at 1x1x2 mm,
+# K = 5, 1024x768 detector at 0.388 mm, 300 views, irregular trace (period
+# 3-6 s, amplitude 8-20 mm, 5 mm drift); model and CT stored in float32,
+# bfloat16 and float16 in turn.
+PRECISION = dict(name="precision-512x512x160-K5-1024x768", vol=(512, 512, 160, 1.0, 1.0, 2.0), K=5,
+                 det=(1024, 768, 0.388, 0.388), n_proj=300, fps=10.0, period_s=4.5, amp_mm=14.0,
+                 jitter=1.0 / 3.0, amp_jitter=3.0 / 7.0, drift_mm=5.0, tumor_mm=20.0,
+                 seeds=dict(phantom=30, dvf=31, noise=32, trace=33), noise=0.01)
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -42,6 +51,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--irregular", action="store_true", help="irregular breathing trace")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="sequence", choices=["sequence", "precision"],
+                    help="sequence: the default line; precision: float32 vs bfloat16 vs float16 storage")
     return ap.parse_args()
 
 
@@ -422,6 +433,115 @@ def run_reference(args, ws_, rank):
                     "d2h_bytes_per_step": 0}}
 
 
+# ------------------------------------------------------- precision workload
+def run_precision(args, local):
+    import torch
+
+    from paper_1102_1712_gb300 import build as B
+    from paper_1102_1712_gb300 import pcasolve as P
+    from paper_1102_1712_gb300 import synth as S
+
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    W = PRECISION
+    vol = S.volume(*W["vol"])
+    f0, c_ref = S.phantom(vol, W["tumor_mm"], seed=W["seeds"]["phantom"])
+    U = S.eigen_dvfs(vol, W["K"], seed=W["seeds"]["dvf"], coarse=(2, 4, 4))
+    trace = S.breathing_trace(W["n_proj"], W["fps"], W["period_s"], W["amp_mm"], K=W["K"], irregular=True,
+                              drift_mm=W["drift_mm"], jitter=W["jitter"], amp_jitter=W["amp_jitter"],
+                              seed=W["seeds"]["trace"])
+    train = S.breathing_trace(400, W["fps"], W["period_s"], W["amp_mm"], K=W["K"], t0=0.37)
+    angles = S.gantry_angles(W["n_proj"], 360.0)
+    d = W["det"]
+    views = [S.cone_beam(d[0], d[1], d[2], d[3], float(a)) for a in angles]
+    step = 0.5 * min(W["vol"][3:])
+    K, M = W["K"], d[0] * d[1]
+    W_, K_ = args.warmup, args.steps
+    n_used = W_ + K_
+    tf0 = torch.from_numpy(f0.ravel()).to(dev)
+    tU = torch.from_numpy(U.ravel()).to(dev)
+    ys = torch.empty((n_used, M), dtype=torch.float32, device=dev)
+    c_true = np.zeros((n_used, 3))
+    for t in range(n_used):
+        p = P.drr_forward(P.warp_volume(tf0, P.pca_dvf(None, tU, trace[t], vol), vol), vol, views[t], step)
+        sigma = W["noise"] * float(p.abs().max())
+        ys[t] = p + torch.from_numpy(S.gaussian_noise(M, sigma, seed=1000 * W["seeds"]["noise"] + t)).to(dev)
+        c_true[t], _ = P.localize_tumor(None, tU, trace[t], vol, c_ref)
+    c_lp = P.lp_fit(train, 2)
+    prm = P.default_params(step)
+    wsp = P.Workspace(vol, views[0], K, device=dev)
+    kb = kernel_bytes(f0.size, M, K, False)
+    out = {}
+    pk, pk_kind = peaks()
+    for name, dt in [("float32", torch.float32), ("bfloat16", torch.bfloat16), ("float16", torch.float16)]:
+        sf0, sU = tf0.to(dt), tU.to(dt)
+        hist = []
+
+        def solve(t, rec):
+            w0 = np.zeros(K) if t == 0 else hist[-1] if t == 1 else P.lp_predict(np.stack([hist[-1], hist[-2]]), c_lp)
+            w, st = P.solve_projection(sf0, None, sU, ys[t], vol, views[t], w0, prm, ws=wsp)
+            c, _ = P.localize_tumor(None, sU, w, vol, c_ref)
+            hist.append(w)
+            rec.append((t, st, c))
+
+        warm, timed = [], []
+        for t in range(W_):
+            solve(t, warm)
+        torch.cuda.synchronize()
+        P.profile(True)
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for t in range(W_, n_used):
+                solve(t, timed)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        prof = P.profile_read()
+        P.profile(False)
+        errs = np.array([np.linalg.norm(c - c_true[t]) for t, _, c in timed])
+        # model and CT bytes scale with the storage size (warp and Jacobian passes)
+        scale = {"float32": 1.0, "bfloat16": 0.5, "float16": 0.5}[name]
+        kern = {}
+        for kname in ("warp_pca", "warp_batch", "drr_solver", "drr_batch", "resid", "adjoint_grad"):
+            n, tot = prof[kname]
+            if n:
+                by = kb[kname]
+                if kname in ("warp_pca", "warp_batch", "adjoint_grad"):
+                    by = int(by - (1.0 - scale) * (12 * K + 4) * f0.size)
+                kern[kname] = {"launches": n, "avg_ms": round(tot / n, 4), "share": round(tot / ms, 4),
+                               "achieved_gbs": round(by / (tot / n * 1e-3) / 1e9, 1)}
+        out[name] = {"value": round(K_ / (ms / 1e3), 3), "ms_per_step": round(ms / K_, 4),
+                     "mm_error": {"mean": round(float(errs.mean()), 4), "p95": round(float(np.percentile(errs, 95)), 4),
+                                  "max": round(float(errs.max()), 4)},
+                     "kernels": kern, "clocks": clk.summary(),
+                     "centroids": [c.tolist() for _, _, c in timed]}
+        del sf0, sU
+    # 16-bit storage against float32 at the same projections
+    cf = np.array(out["float32"].pop("centroids"))
+    for name in ("bfloat16", "float16"):
+        cl = np.array(out[name].pop("centroids"))
+        out[name]["centroid_vs_float32_mm_max"] = round(float(np.abs(cl - cf).max()), 5)
+    bf = out["bfloat16"]
+    dom = max(bf["kernels"], key=lambda k: bf["kernels"][k]["share"])
+    return {"metric": METRIC, "value": bf["value"], "unit": "projections/s", "n_gpus": 1, "steps": K_,
+            "warmup": W_, "ms_per_step": bf["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16 storage, f32 arithmetic",
+            "data": "synthetic (seeded phantom, coarse-grid smoothed eigen-DVFs, irregular trace; "
+                    "projections rendered by this library in float32 + 1% noise)",
+            "config": {"workload": W["name"], "volume": "512x512x160 @ 1x1x2 mm", "K": K,
+                       "detector": "1024x768 @ 0.388 mm", "step_mm": step,
+                       "projections": f"{W_}+{K_} of 300 over 360 deg, irregular"},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": bf["kernels"][dom]["achieved_gbs"],
+                         "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": round(bf["kernels"][dom]["achieved_gbs"] / pk["hbm_gbs"], 4),
+                         "traffic": None, "peak_source": pk_kind},
+            "storage": out, "clocks": bf["clocks"]}
+
+
 def main():
     args = parse()
     ws_, rank, local = dist_env()
@@ -430,6 +550,8 @@ def main():
         torch.distributed.init_process_group("nccl")
     if args.impl == "reference":
         line = run_reference(args, ws_, rank)
+    elif args.workload == "precision":
+        line = run_precision(args, local) if rank == 0 else None
     else:
         line = run_ours(args, ws_, rank, local)
     if line is not None:
