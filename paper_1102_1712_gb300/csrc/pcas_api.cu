@@ -152,7 +152,7 @@ int check_model(const void* mean, const void* U, int K) {
 
 // ------------------------------------------------------------- workspace
 struct Layout {
-    size_t state, fpad, fpad4, pbuf, rayt, part_drr, part_res, part_adj, act_idx, act_h, tile_count,
+    size_t state, view, fpad, fpad4, pbuf, rayt, part_drr, part_res, part_adj, act_idx, act_h, tile_count,
         tile_off, total;
 };
 
@@ -163,6 +163,7 @@ Layout layout(const pcas_vol* vol, const pcas_cb* cb, int K) {
     size_t M = (size_t)cb->nu * cb->nv;
     size_t off = 0;
     L.state = off; off += align256(sizeof(SolveState));
+    L.view = off; off += align256(sizeof(View));
     L.fpad = off; off += align256(npad * sizeof(float));                 // f(w), zero halo
     L.fpad4 = off; off += align256(npad * sizeof(float4));               // four candidates
     L.pbuf = off; off += align256((size_t)NBUF * M * sizeof(float));     // projection ring
@@ -181,6 +182,7 @@ Layout layout(const pcas_vol* vol, const pcas_cb* cb, int K) {
 
 struct Ws {
     SolveState* st;
+    View* view;
     float *fpad, *pbuf;
     float4 *fpad4, *rayt;
     double *part_drr, *part_res, *part_adj;
@@ -196,6 +198,7 @@ int bind_ws(void* ws, size_t ws_bytes, const pcas_vol* vol, const pcas_cb* cb, i
         return fail(PCAS_ERR_INVALID_ARG, "workspace too small: %zu < %zu bytes", ws_bytes, L.total);
     char* b = static_cast<char*>(ws);
     W->st = reinterpret_cast<SolveState*>(b + L.state);
+    W->view = reinterpret_cast<View*>(b + L.view);
     W->fpad = reinterpret_cast<float*>(b + L.fpad);
     W->fpad4 = reinterpret_cast<float4*>(b + L.fpad4);
     W->pbuf = reinterpret_cast<float*>(b + L.pbuf);
@@ -281,7 +284,7 @@ __global__ void k_localize(const T* __restrict__ mean, const T* __restrict__ U, 
 // Reset the solver state for a new evaluation/solve.
 __global__ void k_init_state(SolveState* st, int K, double w0, double w1, double w2, double w3,
                              double w4, double w5, double w6, double w7, double mu0, double alpha,
-                             double beta, double mu_min, int max_trials) {
+                             double beta, double mu_min, int max_trials, int max_iter) {
     if (threadIdx.x != 0) return;
     const double w[PCAS_KMAX] = {w0, w1, w2, w3, w4, w5, w6, w7};
     for (int k = 0; k < PCAS_KMAX; k++) {
@@ -298,9 +301,15 @@ __global__ void k_init_state(SolveState* st, int K, double w0, double w1, double
     st->mu0 = mu0; st->alpha = alpha; st->beta = beta; st->mu_min = mu_min;
     st->K = K; st->max_trials = max_trials;
     st->cur = 0; st->phase = PH_RUNNING; st->evals = 0; st->trials = 0;
+    st->nvalid = 0; st->iters = 0; st->batches = 0; st->max_iter = max_iter;
     for (int i = 0; i < 4; i++) st->counter[i] = 0u;
     for (int i = 0; i < 2; i++)
         for (int j = 0; j < 6; j++) st->box[i][j] = BOX_EMPTY;
+}
+
+int upload_view(View* dst, const View& V, cudaStream_t s) {
+    PCAS_CUDA(cudaMemcpyAsync(dst, &V, sizeof(View), cudaMemcpyHostToDevice, s));
+    return PCAS_OK;
 }
 
 int launch_init(SolveState* st, int K, const double* w, const pcas_params* prm, cudaStream_t s) {
@@ -311,7 +320,7 @@ int launch_init(SolveState* st, int K, const double* w, const pcas_params* prm, 
     PCAS_LAUNCH(PCAS_K_INIT, s,
                 (k_init_state<<<1, 32, 0, s>>>(st, K, v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7],
                                                prm->mu0, prm->alpha, prm->beta, prm->mu_min,
-                                               prm->max_trials),
+                                               prm->max_trials, prm->max_iter),
                  cudaGetLastError()));
     return PCAS_OK;
 }
@@ -349,10 +358,10 @@ int eval_gradient_pipeline(const void* f0, const void* mean, const void* U, int 
     ws.phase = &W.st->phase;
     PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, dt, K, ws, g, pd, W.fpad, W.st->box[0], s));
     PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
-                launch_drr_solver(W.fpad, W.fpad4, g, pd, V, y, W.pbuf, 0, 1, W.st, W.part_drr, s));
-    PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, 1, W.rayt, W.st, W.part_res, s));
+                launch_drr_solver(W.fpad, W.fpad4, g, pd, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, s));
+    PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, W.view, 1, W.rayt, W.st, W.part_res, s));
     PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
-                launch_adjoint_grad(W.rayt, g, V, f0, mean, U, dt, K, step_setup, W.st, W.part_adj, W.adj,
+                launch_adjoint_grad(W.rayt, g, W.view, f0, mean, U, dt, K, step_setup, W.st, W.part_adj, W.adj,
                                     adjoint_block_cap(), s));
     return PCAS_OK;
 }
@@ -477,6 +486,7 @@ int cost_grad_typed(const void* f0, const void* mean, const void* U, int dtype, 
     Pad pd = make_pad(vol->nx, vol->ny, vol->nz);
     PCAS_CUDA(cudaMemsetAsync(W.fpad, 0, W.fpad_bytes, s));
     PCAS_TRY(launch_init(W.st, K, w, nullptr, s));
+    PCAS_TRY(upload_view(W.view, V, s));
     PCAS_TRY(eval_gradient_pipeline(f0, mean, U, dtype, K, y, g, pd, V, W, 0, s));
     SolveState h;
     PCAS_CUDA(cudaMemcpyAsync(&h, W.st, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -531,19 +541,20 @@ int cost_grad_f0(const float* f0, const float* mean, const float* U, int K, cons
     Pad pd = make_pad(vol->nx, vol->ny, vol->nz);
     PCAS_CUDA(cudaMemsetAsync(W.fpad, 0, W.fpad_bytes, s));
     PCAS_TRY(launch_init(W.st, K, w, nullptr, s));
+    PCAS_TRY(upload_view(W.view, V, s));
     WSrc wsrc{};
     wsrc.dev = W.st->w;
     wsrc.phase = &W.st->phase;
     PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, DT_F32, K, wsrc, g, pd, W.fpad, W.st->box[0], s));
     PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
-                launch_drr_solver(W.fpad, W.fpad4, g, pd, V, y, W.pbuf, 0, 1, W.st, W.part_drr, s));
-    PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, 1, W.rayt, W.st, W.part_res, s));
+                launch_drr_solver(W.fpad, W.fpad4, g, pd, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, s));
+    PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, W.view, 1, W.rayt, W.st, W.part_res, s));
     if (dJdw)
         PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
-                    launch_adjoint_grad(W.rayt, g, V, f0, mean, U, DT_F32, K, 0, W.st, W.part_adj, W.adj,
+                    launch_adjoint_grad(W.rayt, g, W.view, f0, mean, U, DT_F32, K, 0, W.st, W.part_adj, W.adj,
                                         adjoint_block_cap(), s));
     if (dJdf0)
-        PCAS_LAUNCH(PCAS_K_GRAD_F0, s, launch_grad_f0(W.rayt, g, V, mean, U, K, W.st, z, zmax, acc, dJdf0, s));
+        PCAS_LAUNCH(PCAS_K_GRAD_F0, s, launch_grad_f0(W.rayt, g, W.view, mean, U, K, W.st, z, zmax, acc, dJdf0, s));
     SolveState h;
     PCAS_CUDA(cudaMemcpyAsync(&h, W.st, sizeof(h), cudaMemcpyDeviceToHost, s));
     PCAS_CUDA(cudaStreamSynchronize(s));
@@ -582,19 +593,21 @@ int solve_projection_typed(const void* f0, const void* mean, const void* U, int 
     const int adj_cap = adjoint_block_cap();
     PCAS_CUDA(cudaMemsetAsync(W.fpad, 0, W.fpad_bytes + W.fpad4_bytes, s));   // zero halos
     PCAS_TRY(launch_init(W.st, K, w_init, prm, s));
+    PCAS_TRY(upload_view(W.view, V, s));
     WSrc wcur{}, wtrial{};
     wcur.dev = W.st->w;
     wcur.phase = &W.st->phase;
     wtrial.dev = W.st->wt[0];
     wtrial.phase = &W.st->phase;
+    wtrial.nvalid = &W.st->nvalid;
     PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, dtype, K, wcur, g, pd, W.fpad, W.st->box[0], s));
     PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
-                launch_drr_solver(W.fpad, W.fpad4, g, pd, V, y, W.pbuf, 0, 1, W.st, W.part_drr, s));
+                launch_drr_solver(W.fpad, W.fpad4, g, pd, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, s));
     int iters = 0, phase = PH_RUNNING;
     for (int it = 0; it < prm->max_iter; it++) {
-        PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, it == 0, W.rayt, W.st, W.part_res, s));
+        PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, W.view, it == 0, W.rayt, W.st, W.part_res, s));
         PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
-                    launch_adjoint_grad(W.rayt, g, V, f0, mean, U, dtype, K, 1, W.st, W.part_adj, W.adj, adj_cap, s));
+                    launch_adjoint_grad(W.rayt, g, W.view, f0, mean, U, dtype, K, 1, W.st, W.part_adj, W.adj, adj_cap, s));
         // Armijo backtracking over the schedule mu0, beta mu0, ...: the next (up
         // to four) step sizes that the rule may still try are rendered and
         // tested in one pass; the device accepts the first that passes, in
@@ -603,7 +616,7 @@ int solve_projection_typed(const void* f0, const void* mean, const void* U, int 
         double mu_t = prm->mu0;
         int t = 0;
         phase = PH_RUNNING;
-        while (true) {
+        for (int batch = 0; batch <= prm->max_trials; batch++) {    // each batch tries >= 1 step
             int nvalid = 0;
             double m = mu_t;
             while (nvalid < TRIAL_BATCH && m >= prm->mu_min && t + nvalid < prm->max_trials) {
@@ -619,12 +632,12 @@ int solve_projection_typed(const void* f0, const void* mean, const void* U, int 
             if (nvalid >= 2) {
                 PCAS_LAUNCH(PCAS_K_WARP_BATCH, s, launch_warp_batch(f0, mean, U, dtype, K, W.st, g, pd, W.fpad4, s));
                 PCAS_LAUNCH(PCAS_K_DRR_BATCH, s,
-                            launch_drr_solver(W.fpad, W.fpad4, g, pd, V, y, W.pbuf, TRIAL_BATCH, nvalid,
+                            launch_drr_solver(W.fpad, W.fpad4, g, pd, V, W.view, y, W.pbuf, TRIAL_BATCH,
                                               W.st, W.part_drr, s));
             } else {
                 PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, dtype, K, wtrial, g, pd, W.fpad, W.st->box[0], s));
                 PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
-                            launch_drr_solver(W.fpad, W.fpad4, g, pd, V, y, W.pbuf, 1, 1, W.st, W.part_drr, s));
+                            launch_drr_solver(W.fpad, W.fpad4, g, pd, V, W.view, y, W.pbuf, 1, W.st, W.part_drr, s));
             }
             PCAS_CUDA(cudaMemcpyAsync(&phase, &W.st->phase, sizeof(int), cudaMemcpyDeviceToHost, s));
             PCAS_CUDA(cudaStreamSynchronize(s));

@@ -76,6 +76,9 @@ struct SolveState {
     int K, max_trials;
     int cur;                              // buffer holding P f(w)
     int phase, evals, trials;
+    int nvalid;                           // candidates of the pending batch still on the schedule
+    int iters, batches;                   // device-driven solve: completed iterations, batches this iteration
+    int max_iter, pad_;
     unsigned int counter[4];              // last-block counters (reset by the last block)
     // Bounding box of the non-zero voxels of the warped volume (slot 0: f,
     // slot 1: the union of the four candidates), as {xmin, ymin, zmin, -xmax,
@@ -86,6 +89,18 @@ struct SolveState {
 };
 
 enum : int { BOX_EMPTY = 0x3fffffff };
+
+// Number of the next (up to TRIAL_BATCH) step sizes mu, beta mu, ... that the
+// backtracking rule may still try: mu >= mu_min and fewer than max_trials
+// trials in this iteration.  The host mirrors the same loop.
+__host__ __device__ inline int count_valid(double mu, double beta, double mu_min, int trials, int max_trials) {
+    int n = 0;
+    while (n < TRIAL_BATCH && mu >= mu_min && trials + n < max_trials) {
+        n++;
+        mu *= beta;
+    }
+    return n;
+}
 
 // Reduction scratch: per-block partials plus the counter used to find the
 // last block to finish (which then reduces all partials in a fixed order).
@@ -329,6 +344,7 @@ struct WSrc {                 // where a PCA-model kernel takes w from
     float w[PCAS_KMAX];       // used when dev is null
     const double* dev;        // device w (solver state), K doubles
     const int* phase;         // early exit when *phase >= PH_STOP (may be null)
+    const int* nvalid;        // if set: run only for a one-candidate batch (*nvalid == 1)
 };
 
 // Storage type of f0 / mean / U (values of pcas_dtype in pcasolve.h).
@@ -345,12 +361,14 @@ cudaError_t launch_warp_batch(const void* f0, const void* mean, const void* U, i
                               const SolveState* st, Grid g, Pad pd, float4* fpad4, cudaStream_t s);
 cudaError_t launch_drr_plain(const float* f, Grid g, const View& V, float* p, cudaStream_t s);
 // Solver projector.  mode 0: first evaluation into buffer cur; mode 1: one
-// trial volume; mode 4: the four-volume batch (nvalid of them on the schedule).
+// trial volume; mode 4: the four-volume batch (st->nvalid of them on the
+// schedule).  Vh: the view on the host (grid size), Vd: the same in device
+// memory (read by the kernels, so captured launches stay view-independent).
 cudaError_t launch_drr_solver(const float* fpad, const float4* fpad4, Grid g, Pad pd,
-                              const View& V, const float* y, float* pbuf, int mode, int nvalid,
+                              const View& Vh, const View* Vd, const float* y, float* pbuf, int mode,
                               SolveState* st, double* part, cudaStream_t s);
-cudaError_t launch_resid(const float* pbuf, const float* y, const View& V, int first, float4* rayt,
-                         SolveState* st, double* part, cudaStream_t s);
+cudaError_t launch_resid(const float* pbuf, const float* y, const View& Vh, const View* Vd, int first,
+                         float4* rayt, SolveState* st, double* part, cudaStream_t s);
 cudaError_t launch_adjoint_plain(const float* img, Grid g, const View& V, float* gout,
                                  cudaStream_t s);
 // Scratch of the gradient pass: compacted voxels with a non-zero warp
@@ -362,13 +380,13 @@ struct AdjScratch {
     int* tile_off;      // ntiles + 1
 };
 inline long adj_tiles(int nx, int ny, int nz) { return (long)((nx + 7) / 8) * ((ny + 7) / 8) * ((nz + 3) / 4); }
-cudaError_t launch_adjoint_grad(const float4* rayt, Grid g, const View& V, const void* f0,
+cudaError_t launch_adjoint_grad(const float4* rayt, Grid g, const View* V, const void* f0,
                                 const void* mean, const void* U, int dt, int K, int step_setup,
                                 SolveState* st, double* part, const AdjScratch& as, int max_blocks,
                                 cudaStream_t s);
 // dJ/df0 = W^T (2 P^T r): z (N floats) and acc (N 64-bit) are scratch,
 // zmax_bits one word; out (N floats) receives the gradient.
-cudaError_t launch_grad_f0(const float4* rayt, Grid g, const View& V, const float* mean, const float* U,
+cudaError_t launch_grad_f0(const float4* rayt, Grid g, const View* V, const float* mean, const float* U,
                            int K, const SolveState* st, float* z, unsigned int* zmax_bits,
                            unsigned long long* acc, float* out, cudaStream_t s);
 cudaError_t launch_localize(const float* mean, const float* U, int K, const double* w, Grid g,

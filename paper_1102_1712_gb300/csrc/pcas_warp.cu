@@ -103,6 +103,7 @@ k_warp_pca(const T* __restrict__ f0, const T* __restrict__ mean,
            const T* __restrict__ U, int K, WSrc ws, Grid g, Pad pd, long N,
            float* __restrict__ fpad, int* __restrict__ box_out) {
     if (ws.phase && *ws.phase >= PH_STOP) return;
+    if (ws.nvalid && *ws.nvalid != 1) return;
     __shared__ float s_w[PCAS_KMAX];
     if (threadIdx.x < PCAS_KMAX)
         s_w[threadIdx.x] = ws.dev ? (threadIdx.x < K ? (float)ws.dev[threadIdx.x] : 0.f)
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(kWarpThreads)
 k_warp_batch(const T* __restrict__ f0, const T* __restrict__ mean,
              const T* __restrict__ U, int K, const SolveState* st, Grid g, Pad pd, long N,
              float4* __restrict__ fpad4, int* __restrict__ box_out) {
-    if (st->phase >= PH_STOP) return;
+    if (st->phase >= PH_STOP || st->nvalid < 2) return;
     __shared__ float s_w[TRIAL_BATCH][PCAS_KMAX];
     if (threadIdx.x < TRIAL_BATCH * PCAS_KMAX) {
         const int j = threadIdx.x / PCAS_KMAX, k = threadIdx.x % PCAS_KMAX;
