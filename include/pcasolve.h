@@ -181,6 +181,47 @@ int localize_tumor(const float* mean, const float* U, int K, const double* w,
                    double c_out[3], void* stream);
 
 /* ------------------------------------------------------------------------
+ * Device-driven solves (the Appendix loop without host round trips).
+ * A pcas_solver captures solve_projection for one reference CT, motion model
+ * and detector shape as a CUDA graph whose iteration and backtracking loops
+ * are conditional WHILE nodes driven by the device state; solving a
+ * projection is one graph launch.  Results equal solve_projection's (same
+ * kernels, same order of operations).
+ *
+ * pcas_solver_create: f0, mean, U (storage dtype as the *_typed calls) and
+ *   the workspace (pcas_solver_workspace_bytes, device, 256-byte aligned) are
+ *   owned by the caller and must stay valid until destroy; cb gives the
+ *   detector shape (its angle and offsets are per-solve); params are fixed.
+ *   Allocates pinned host staging buffers and builds the graph; not for
+ *   use inside stream capture.
+ * pcas_solver_solve: y (device, [nv][nu]) is copied into the solver's image
+ *   buffer unless it is that buffer (pcas_solver_y_buffer) or NULL; the view
+ *   is the creation view with this angle and these detector offsets.
+ *   w_init, w_out (K), stats: host.  Synchronous.  One solver must not be
+ *   used by two host threads at once.
+ * pcas_batch_create: one graph holding the solves of n solvers as independent
+ *   branches (uneven sizes allowed), each preceded by a copy from y_src[i]
+ *   (device, may be NULL: the solver's own buffer is used).
+ * pcas_batch_solve: one graph launch for all n; angle_rad[i] per solve;
+ *   w_init and w_out are n x PCAS_KMAX host arrays (row i, first K_i
+ *   entries); stats[i] per solve (status set per solve).  Synchronous. */
+typedef struct pcas_solver_s* pcas_solver;
+typedef struct pcas_batch_s* pcas_batch;
+size_t pcas_solver_workspace_bytes(const pcas_vol* vol, const pcas_cb* cb, int K);
+int pcas_solver_create(pcas_solver* out, const void* f0, const void* mean, const void* U, int dtype,
+                       int K, const pcas_vol* vol, const pcas_cb* cb, const pcas_params* params,
+                       void* ws, size_t ws_bytes, void* stream);
+float* pcas_solver_y_buffer(pcas_solver solver);
+int pcas_solver_solve(pcas_solver solver, const float* y, double angle_rad, double off_u, double off_v,
+                      const double* w_init, double* w_out, pcas_stats* stats, void* stream);
+int pcas_solver_destroy(pcas_solver solver);
+int pcas_batch_create(pcas_batch* out, const pcas_solver* solvers, const float* const* y_src, int n,
+                      void* stream);
+int pcas_batch_solve(pcas_batch batch, const double* angle_rad, const double* w_init, double* w_out,
+                     pcas_stats* stats, void* stream);
+int pcas_batch_destroy(pcas_batch batch);
+
+/* ------------------------------------------------------------------------
  * Storage precision of the reference CT and the motion model.  The *_typed
  * calls take f0, mean and U as float (PCAS_F32), bfloat16 (PCAS_BF16) or half
  * (PCAS_F16) arrays with the layouts above; every value is widened to float
@@ -232,7 +273,8 @@ enum {
     PCAS_K_WARP_BATCH = 10,  /* four line-search candidates warped at once      */
     PCAS_K_DRR_BATCH = 11,   /* four candidates projected and tested at once    */
     PCAS_K_GRAD_F0 = 12,     /* dJ/df0: full backprojection + warp transpose    */
-    PCAS_K_COUNT = 13
+    PCAS_K_GRAPH = 13,       /* kernels run inside device-driven (graph) solves  */
+    PCAS_K_COUNT = 14
 };
 int pcas_profile(int on);
 int pcas_profile_read(int kind, long long* launches, double* total_ms);

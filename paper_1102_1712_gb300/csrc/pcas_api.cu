@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <vector>
 
 #include "pcas_internal.cuh"
 
@@ -301,7 +302,7 @@ __global__ void k_init_state(SolveState* st, int K, double w0, double w1, double
     st->mu0 = mu0; st->alpha = alpha; st->beta = beta; st->mu_min = mu_min;
     st->K = K; st->max_trials = max_trials;
     st->cur = 0; st->phase = PH_RUNNING; st->evals = 0; st->trials = 0;
-    st->nvalid = 0; st->iters = 0; st->batches = 0; st->max_iter = max_iter;
+    st->nvalid = 0; st->iters = 0; st->batches = 0; st->max_iter = max_iter; st->launches = 0;
     for (int i = 0; i < 4; i++) st->counter[i] = 0u;
     for (int i = 0; i < 2; i++)
         for (int j = 0; j < 6; j++) st->box[i][j] = BOX_EMPTY;
@@ -822,6 +823,411 @@ int lp_predict(const double* hist, const double* c, int K, int L, double* w0) {
         for (int l = 0; l < L; l++) acc += c[k * L + l] * hist[(long)l * K + k];
         w0[k] = acc;
     }
+    return PCAS_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Device-driven solve: the loop of the Appendix as one CUDA graph.  Two nested
+// conditional WHILE nodes replace the host loop -- iterations, and candidate
+// batches inside an iteration -- and one-thread controller kernels set their
+// conditions from the solver state.  Both loops are bounded by construction:
+// an iteration either accepts a step (at most max_iter of them) or ends the
+// solve, and every batch tries at least one step size of the iteration's
+// schedule (at most max_trials).  The view and the initial coefficients come
+// from pinned host buffers through memcpy nodes, so one instantiated graph
+// serves every gantry angle.
+// ===========================================================================
+namespace {
+
+struct InitBlock {
+    double w[PCAS_KMAX];
+    double mu0, alpha, beta, mu_min;
+    int K, max_trials, max_iter, pad;
+};
+
+__global__ void k_init_dev(SolveState* st, const InitBlock* __restrict__ ib) {
+    if (threadIdx.x != 0) return;
+    for (int k = 0; k < PCAS_KMAX; k++) {
+        st->w[k] = k < ib->K ? ib->w[k] : 0.0;
+        st->d[k] = 0.0;
+        st->G[k] = 0.0;
+        for (int j = 0; j < TRIAL_BATCH; j++) st->wt[j][k] = st->w[k];
+    }
+    for (int j = 0; j < TRIAL_BATCH; j++) st->mu_batch[j] = 0.0;
+    st->gnorm = st->a = st->b = st->J = st->J0 = st->Jt = 0.0;
+    st->mu = ib->mu0;
+    for (int i = 0; i < NBUF; i++)
+        for (int j = 0; j < NMOM; j++) st->mom[i][j] = 0.0;
+    st->mu0 = ib->mu0; st->alpha = ib->alpha; st->beta = ib->beta; st->mu_min = ib->mu_min;
+    st->K = ib->K; st->max_trials = ib->max_trials; st->max_iter = ib->max_iter;
+    st->cur = 0; st->phase = PH_RUNNING; st->evals = 0; st->trials = 0;
+    st->nvalid = 0; st->iters = 0; st->batches = 0; st->launches = 1;
+    for (int i = 0; i < 4; i++) st->counter[i] = 0u;
+    for (int i = 0; i < 2; i++)
+        for (int j = 0; j < 6; j++) st->box[i][j] = BOX_EMPTY;
+}
+
+// After the first evaluation (init, warp, projection, this kernel).
+__global__ void k_ctrl_start(SolveState* st, cudaGraphConditionalHandle h_outer) {
+    st->launches += 3;
+    cudaGraphSetConditional(h_outer, (st->max_iter > 0 && st->phase < PH_STOP) ? 1u : 0u);
+}
+
+// Inside an iteration, after the gradient: run candidate batches while the line search is open.
+__global__ void k_ctrl_batches(SolveState* st, cudaGraphConditionalHandle h_inner) {
+    st->batches = 0;
+    cudaGraphSetConditional(h_inner, st->phase == PH_RUNNING ? 1u : 0u);
+}
+
+// End of a candidate batch (two warps, two projections -- one pair runs -- and this kernel).
+__global__ void k_ctrl_batch_end(SolveState* st, cudaGraphConditionalHandle h_inner) {
+    st->batches += 1;
+    st->launches += 5;
+    const bool more = st->phase == PH_RUNNING && st->batches <= st->max_trials;
+    cudaGraphSetConditional(h_inner, more ? 1u : 0u);
+}
+
+// End of an iteration (residual, three gradient kernels, batch start, this kernel).
+__global__ void k_ctrl_iter_end(SolveState* st, cudaGraphConditionalHandle h_outer) {
+    st->launches += 6;
+    int ph = st->phase;
+    if (ph == PH_RUNNING) {          // batch cap reached without a decision: end the solve
+        ph = PH_STOP;
+        st->phase = ph;
+    }
+    if (ph == PH_ACCEPT || ph == PH_STOP) st->iters += 1;
+    const bool more = ph == PH_ACCEPT && st->iters < st->max_iter;
+    cudaGraphSetConditional(h_outer, more ? 1u : 0u);
+}
+
+#define PCAS_G(call)                                                                              \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) {                                                                  \
+            cudaGraph_t g_junk;                                                                   \
+            cudaStreamEndCapture(cs, &g_junk);                                                    \
+            return fail(PCAS_ERR_CUDA, "graph build: %s failed: %s", #call, cudaGetErrorString(e_)); \
+        }                                                                                         \
+    } while (0)
+
+// Adds a WHILE node after the current capture position and moves the capture past it.
+int add_while(cudaStream_t cs, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+    cudaStreamCaptureStatus status;
+    cudaGraph_t g;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    PCAS_G(cudaStreamGetCaptureInfo(cs, &status, nullptr, &g, &deps, nullptr, &ndeps));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    PCAS_G(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp));
+    *body = cp.conditional.phGraph_out[0];
+    PCAS_G(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return PCAS_OK;
+}
+
+}  // namespace
+
+struct pcas_solver_s {
+    int device;
+    pcas_vol vol;
+    pcas_cb cb;
+    pcas_params prm;
+    int K, dtype;
+    const void *f0, *mean, *U;
+    Ws W;
+    float* y;             // device, M floats (in the workspace)
+    InitBlock* d_init;    // device (in the workspace)
+    View* h_view;         // pinned host staging
+    InitBlock* h_init;
+    SolveState* h_state;
+    cudaGraphConditionalHandle h_outer, h_inner;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    View view0;           // geometry at creation (grid sizes)
+};
+
+struct pcas_batch_s {
+    std::vector<pcas_solver> solvers;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+namespace {
+
+size_t solver_extra(const pcas_cb* cb) {
+    return align256((size_t)cb->nu * cb->nv * sizeof(float)) + align256(sizeof(InitBlock));
+}
+
+// Captures one device-driven solve into `graph` as an independent branch
+// (optionally preceded by a copy of the measured image from y_src).
+int capture_solve(pcas_solver s, cudaGraph_t graph, cudaStream_t cs, const float* y_src) {
+    const Grid g = make_grid(&s->vol);
+    const Pad pd = make_pad(s->vol.nx, s->vol.ny, s->vol.nz);
+    const Ws& W = s->W;
+    const View& V = s->view0;
+    const size_t M = (size_t)s->cb.nu * s->cb.nv;
+    PCAS_G(cudaGraphConditionalHandleCreate(&s->h_outer, graph, 0, cudaGraphCondAssignDefault));
+    // prologue
+    PCAS_G(cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    if (y_src) PCAS_G(cudaMemcpyAsync(s->y, y_src, M * sizeof(float), cudaMemcpyDeviceToDevice, cs));
+    PCAS_G(cudaMemcpyAsync(W.view, s->h_view, sizeof(View), cudaMemcpyHostToDevice, cs));
+    PCAS_G(cudaMemcpyAsync(s->d_init, s->h_init, sizeof(InitBlock), cudaMemcpyHostToDevice, cs));
+    k_init_dev<<<1, 32, 0, cs>>>(W.st, s->d_init);
+    PCAS_G(cudaGetLastError());
+    WSrc wcur{};
+    wcur.dev = W.st->w;
+    wcur.phase = &W.st->phase;
+    WSrc wtrial = wcur;
+    wtrial.dev = W.st->wt[0];
+    wtrial.nvalid = &W.st->nvalid;
+    PCAS_G(launch_warp_pca(s->f0, s->mean, s->U, s->dtype, s->K, wcur, g, pd, W.fpad, W.st->box[0], cs));
+    PCAS_G(launch_drr_solver(W.fpad, W.fpad4, g, pd, V, W.view, s->y, W.pbuf, 0, W.st, W.part_drr, cs));
+    k_ctrl_start<<<1, 1, 0, cs>>>(W.st, s->h_outer);
+    PCAS_G(cudaGetLastError());
+    cudaGraph_t outer_body;
+    PCAS_TRY(add_while(cs, s->h_outer, &outer_body));
+    cudaGraph_t done;
+    PCAS_G(cudaStreamEndCapture(cs, &done));
+    // one iteration: residual + gradient, then the candidate batches
+    PCAS_G(cudaGraphConditionalHandleCreate(&s->h_inner, outer_body, 0, cudaGraphCondAssignDefault));
+    PCAS_G(cudaStreamBeginCaptureToGraph(cs, outer_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    PCAS_G(launch_resid(W.pbuf, s->y, V, W.view, -1, W.rayt, W.st, W.part_res, cs));
+    PCAS_G(launch_adjoint_grad(W.rayt, g, W.view, s->f0, s->mean, s->U, s->dtype, s->K, 1, W.st, W.part_adj,
+                               W.adj, adjoint_block_cap(), cs));
+    k_ctrl_batches<<<1, 1, 0, cs>>>(W.st, s->h_inner);
+    PCAS_G(cudaGetLastError());
+    cudaGraph_t inner_body;
+    PCAS_TRY(add_while(cs, s->h_inner, &inner_body));
+    k_ctrl_iter_end<<<1, 1, 0, cs>>>(W.st, s->h_outer);
+    PCAS_G(cudaGetLastError());
+    PCAS_G(cudaStreamEndCapture(cs, &done));
+    // one candidate batch: the four-volume pair or the one-volume pair runs
+    PCAS_G(cudaStreamBeginCaptureToGraph(cs, inner_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    PCAS_G(launch_warp_batch(s->f0, s->mean, s->U, s->dtype, s->K, W.st, g, pd, W.fpad4, cs));
+    PCAS_G(launch_drr_solver(W.fpad, W.fpad4, g, pd, V, W.view, s->y, W.pbuf, TRIAL_BATCH, W.st, W.part_drr, cs));
+    PCAS_G(launch_warp_pca(s->f0, s->mean, s->U, s->dtype, s->K, wtrial, g, pd, W.fpad, W.st->box[0], cs));
+    PCAS_G(launch_drr_solver(W.fpad, W.fpad4, g, pd, V, W.view, s->y, W.pbuf, 1, W.st, W.part_drr, cs));
+    k_ctrl_batch_end<<<1, 1, 0, cs>>>(W.st, s->h_inner);
+    PCAS_G(cudaGetLastError());
+    PCAS_G(cudaStreamEndCapture(cs, &done));
+    return PCAS_OK;
+}
+
+#undef PCAS_G
+
+int solver_stage(pcas_solver s, double angle_rad, double off_u, double off_v, const double* w_init) {
+    pcas_cb cb = s->cb;
+    cb.angle_rad = angle_rad;
+    cb.off_u = off_u;
+    cb.off_v = off_v;
+    View V;
+    PCAS_TRY(make_view(&s->vol, &cb, s->prm.step_mm, &V));
+    PCAS_TRY(check_finite(w_init, s->K, "w_init"));
+    *s->h_view = V;
+    InitBlock ib = {};
+    for (int k = 0; k < s->K; k++) ib.w[k] = w_init[k];
+    ib.mu0 = s->prm.mu0; ib.alpha = s->prm.alpha; ib.beta = s->prm.beta; ib.mu_min = s->prm.mu_min;
+    ib.K = s->K; ib.max_trials = s->prm.max_trials; ib.max_iter = s->prm.max_iter;
+    *s->h_init = ib;
+    return PCAS_OK;
+}
+
+int solver_collect(pcas_solver s, double* w_out, pcas_stats* stats) {
+    const SolveState& h = *s->h_state;
+    if (h.phase == PH_SINGULAR) return fail(PCAS_ERR_SINGULAR, "Y^T Y is singular (constant image y)");
+    if (w_out)
+        for (int k = 0; k < s->K; k++) w_out[k] = h.w[k];
+    if (stats) {
+        stats->iters = h.iters;
+        stats->evals = h.evals;
+        stats->status = PCAS_OK;
+        stats->J0 = h.J0;
+        stats->J = h.J;
+        stats->a = h.a;
+        stats->b = h.b;
+        stats->mu_last = h.mu;
+    }
+    return PCAS_OK;
+}
+
+void solver_free(pcas_solver s) {
+    if (!s) return;
+    if (s->exec) cudaGraphExecDestroy(s->exec);
+    if (s->graph) cudaGraphDestroy(s->graph);
+    if (s->h_view) cudaFreeHost(s->h_view);
+    if (s->h_init) cudaFreeHost(s->h_init);
+    if (s->h_state) cudaFreeHost(s->h_state);
+    delete s;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t pcas_solver_workspace_bytes(const pcas_vol* vol, const pcas_cb* cb, int K) {
+    if (check_vol(vol) != PCAS_OK || !cb || cb->nu < 1 || cb->nv < 1 || K < 1 || K > PCAS_KMAX) return 0;
+    return layout(vol, cb, K).total + solver_extra(cb);
+}
+
+int pcas_solver_create(pcas_solver* out, const void* f0, const void* mean, const void* U, int dtype, int K,
+                       const pcas_vol* vol, const pcas_cb* cb, const pcas_params* prm, void* ws,
+                       size_t ws_bytes, void* stream) {
+    PCAS_TRY(check_ptr(out, "out"));
+    *out = nullptr;
+    PCAS_TRY(check_vol(vol));
+    PCAS_TRY(check_model(mean, U, K));
+    PCAS_TRY(check_dtype(dtype));
+    PCAS_TRY(check_ptr(f0, "f0"));
+    PCAS_TRY(check_ptr(prm, "params"));
+    if (!(prm->mu0 > 0) || !(prm->alpha >= 0) || !(prm->beta > 0 && prm->beta < 1) || !(prm->mu_min >= 0) ||
+        prm->max_iter < 0 || prm->max_iter > 100000 || prm->max_trials < 0 || prm->max_trials > 1000)
+        return fail(PCAS_ERR_INVALID_ARG, "solver parameters out of range");
+    View V;
+    PCAS_TRY(make_view(vol, cb, prm->step_mm, &V));
+    const size_t need = pcas_solver_workspace_bytes(vol, cb, K);
+    if (!ws) return fail(PCAS_ERR_INVALID_ARG, "workspace is NULL");
+    if (ws_bytes < need) return fail(PCAS_ERR_INVALID_ARG, "workspace too small: %zu < %zu bytes", ws_bytes, need);
+    const size_t base = layout(vol, cb, K).total;
+    pcas_solver s = new pcas_solver_s();
+    s->vol = *vol; s->cb = *cb; s->prm = *prm; s->K = K; s->dtype = dtype;
+    s->f0 = f0; s->mean = mean; s->U = U; s->view0 = V;
+    int rc = bind_ws(ws, base, vol, cb, K, &s->W);
+    if (rc != PCAS_OK) { solver_free(s); return rc; }
+    char* extra = static_cast<char*>(ws) + base;
+    s->y = reinterpret_cast<float*>(extra);
+    s->d_init = reinterpret_cast<InitBlock*>(extra + align256((size_t)cb->nu * cb->nv * sizeof(float)));
+    cudaStream_t st = as_stream(stream);
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&s->h_view, sizeof(View), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&s->h_init, sizeof(InitBlock), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&s->h_state, sizeof(SolveState), cudaHostAllocDefault);
+    // zero the halos once: the warp kernels never write them
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->W.fpad, 0, s->W.fpad_bytes + s->W.fpad4_bytes, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaGraphCreate(&s->graph, 0);
+    if (e != cudaSuccess) {
+        if (cs) cudaStreamDestroy(cs);
+        solver_free(s);
+        return fail(PCAS_ERR_CUDA, "solver set-up failed: %s", cudaGetErrorString(e));
+    }
+    *s->h_view = V;
+    rc = capture_solve(s, s->graph, cs, nullptr);
+    cudaStreamDestroy(cs);
+    if (rc != PCAS_OK) { solver_free(s); return rc; }
+    e = cudaGraphInstantiate(&s->exec, s->graph, 0);
+    if (e != cudaSuccess) {
+        solver_free(s);
+        return fail(PCAS_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    }
+    *out = s;
+    return PCAS_OK;
+}
+
+float* pcas_solver_y_buffer(pcas_solver s) { return s ? s->y : nullptr; }
+
+int pcas_solver_solve(pcas_solver s, const float* y, double angle_rad, double off_u, double off_v,
+                      const double* w_init, double* w_out, pcas_stats* stats, void* stream) {
+    PCAS_TRY(check_ptr(s, "solver"));
+    PCAS_TRY(check_ptr(w_init, "w_init"));
+    PCAS_TRY(solver_stage(s, angle_rad, off_u, off_v, w_init));
+    cudaStream_t st = as_stream(stream);
+    const size_t M = (size_t)s->cb.nu * s->cb.nv;
+    if (y && y != s->y) PCAS_CUDA(cudaMemcpyAsync(s->y, y, M * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    PCAS_CUDA(cudaGraphLaunch(s->exec, st));
+    PCAS_CUDA(cudaMemcpyAsync(s->h_state, s->W.st, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
+    PCAS_CUDA(cudaStreamSynchronize(st));
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mutex);
+        g_launches[PCAS_K_GRAPH] += s->h_state->launches;
+    }
+    return solver_collect(s, w_out, stats);
+}
+
+int pcas_solver_destroy(pcas_solver s) {
+    solver_free(s);
+    return PCAS_OK;
+}
+
+int pcas_batch_create(pcas_batch* out, const pcas_solver* solvers, const float* const* y_src, int n,
+                      void* stream) {
+    PCAS_TRY(check_ptr(out, "out"));
+    *out = nullptr;
+    PCAS_TRY(check_ptr(solvers, "solvers"));
+    if (n < 1 || n > 4096) return fail(PCAS_ERR_INVALID_ARG, "batch size must be in [1, 4096]");
+    for (int i = 0; i < n; i++)
+        if (!solvers[i]) return fail(PCAS_ERR_INVALID_ARG, "solver %d is NULL", i);
+    (void)stream;
+    pcas_batch b = new pcas_batch_s();
+    b->solvers.assign(solvers, solvers + n);
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaGraphCreate(&b->graph, 0);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        if (b->graph) cudaGraphDestroy(b->graph);
+        delete b;
+        return fail(PCAS_ERR_CUDA, "batch set-up failed: %s", cudaGetErrorString(e));
+    }
+    int rc = PCAS_OK;
+    for (int i = 0; i < n && rc == PCAS_OK; i++) rc = capture_solve(solvers[i], b->graph, cs, y_src ? y_src[i] : nullptr);
+    cudaStreamDestroy(cs);
+    if (rc == PCAS_OK) {
+        e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+        if (e != cudaSuccess) rc = fail(PCAS_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    }
+    if (rc != PCAS_OK) {
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        cudaGraphDestroy(b->graph);
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return PCAS_OK;
+}
+
+int pcas_batch_solve(pcas_batch b, const double* angle_rad, const double* w_init, double* w_out,
+                     pcas_stats* stats, void* stream) {
+    PCAS_TRY(check_ptr(b, "batch"));
+    PCAS_TRY(check_ptr(angle_rad, "angle_rad"));
+    PCAS_TRY(check_ptr(w_init, "w_init"));
+    const int n = (int)b->solvers.size();
+    for (int i = 0; i < n; i++)
+        PCAS_TRY(solver_stage(b->solvers[i], angle_rad[i], b->solvers[i]->cb.off_u, b->solvers[i]->cb.off_v,
+                              w_init + (size_t)i * PCAS_KMAX));
+    cudaStream_t st = as_stream(stream);
+    PCAS_CUDA(cudaGraphLaunch(b->exec, st));
+    for (int i = 0; i < n; i++)
+        PCAS_CUDA(cudaMemcpyAsync(b->solvers[i]->h_state, b->solvers[i]->W.st, sizeof(SolveState),
+                                  cudaMemcpyDeviceToHost, st));
+    PCAS_CUDA(cudaStreamSynchronize(st));
+    int rc = PCAS_OK;
+    long long launches = 0;
+    for (int i = 0; i < n; i++) {
+        launches += b->solvers[i]->h_state->launches;
+        int r = solver_collect(b->solvers[i], w_out ? w_out + (size_t)i * PCAS_KMAX : nullptr,
+                               stats ? stats + i : nullptr);
+        if (stats && r != PCAS_OK) stats[i].status = r;
+        if (r != PCAS_OK && rc == PCAS_OK) rc = r;
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mutex);
+        g_launches[PCAS_K_GRAPH] += launches;
+    }
+    return rc;
+}
+
+int pcas_batch_destroy(pcas_batch b) {
+    if (!b) return PCAS_OK;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    delete b;
     return PCAS_OK;
 }
 

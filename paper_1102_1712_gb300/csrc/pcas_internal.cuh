@@ -78,7 +78,7 @@ struct SolveState {
     int phase, evals, trials;
     int nvalid;                           // candidates of the pending batch still on the schedule
     int iters, batches;                   // device-driven solve: completed iterations, batches this iteration
-    int max_iter, pad_;
+    int max_iter, launches;               // launches: kernels run by a device-driven solve
     unsigned int counter[4];              // last-block counters (reset by the last block)
     // Bounding box of the non-zero voxels of the warped volume (slot 0: f,
     // slot 1: the union of the four candidates), as {xmin, ymin, zmin, -xmax,

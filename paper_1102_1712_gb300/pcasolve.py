@@ -85,13 +85,24 @@ _SIGS = {
     "localize_tumor": (C.c_int, [_P, _P, C.c_int, _D, C.POINTER(Vol), _D, C.c_int, C.c_double, _D, _P]),
     "lp_fit": (C.c_int, [_D, C.c_int, C.c_int, C.c_int, _D]),
     "lp_predict": (C.c_int, [_D, _D, C.c_int, C.c_int, _D]),
+    "pcas_solver_workspace_bytes": (C.c_size_t, [C.POINTER(Vol), C.POINTER(CB), C.c_int]),
+    "pcas_solver_create": (C.c_int, [C.POINTER(C.c_void_p), _P, _P, _P, C.c_int, C.c_int, C.POINTER(Vol),
+                                     C.POINTER(CB), C.POINTER(Params), _P, C.c_size_t, _P]),
+    "pcas_solver_y_buffer": (C.c_void_p, [C.c_void_p]),
+    "pcas_solver_solve": (C.c_int, [C.c_void_p, _P, C.c_double, C.c_double, C.c_double, _D, _D,
+                                    C.POINTER(Stats), _P]),
+    "pcas_solver_destroy": (C.c_int, [C.c_void_p]),
+    "pcas_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                    C.c_int, _P]),
+    "pcas_batch_solve": (C.c_int, [C.c_void_p, _D, _D, _D, C.POINTER(Stats), _P]),
+    "pcas_batch_destroy": (C.c_int, [C.c_void_p]),
     "pcas_profile": (C.c_int, [C.c_int]),
     "pcas_profile_read": (C.c_int, [C.c_int, C.POINTER(C.c_longlong), _D]),
 }
 
 # kernel classes of pcas_profile_read (include/pcasolve.h)
 KERNELS = ["warp_pca", "drr_solver", "resid", "adjoint_grad", "drr_forward", "drr_adjoint",
-           "pca_dvf", "warp_volume", "localize", "init", "warp_batch", "drr_batch", "grad_f0"]
+           "pca_dvf", "warp_volume", "localize", "init", "warp_batch", "drr_batch", "grad_f0", "graph"]
 
 
 def lib():
@@ -378,6 +389,103 @@ def lp_predict(hist, c):
     w0 = np.zeros(K)
     _check(lib().lp_predict(h.ctypes.data_as(_D), cc.ctypes.data_as(_D), K, L, w0.ctypes.data_as(_D)))
     return w0
+
+
+class Solver:
+    """Device-driven solve of one reference CT / motion model / detector shape:
+    solve_projection captured as a CUDA graph with conditional loops (see
+    include/pcasolve.h).  Keeps references to the tensors it was built on."""
+
+    def __init__(self, f0, mean, U, vol, cb, params, device=None, stream=None):
+        import torch
+        self.K = _K(U, vol)
+        self.vol, self.cb = vol_struct(vol), cb_struct(cb)
+        self.tensors = (f0, mean, U)
+        N = _nvox(vol)
+        dt = U.dtype
+        n = int(lib().pcas_solver_workspace_bytes(C.byref(self.vol), C.byref(self.cb), self.K))
+        if n == 0:
+            raise ValueError("invalid volume / view / K")
+        self.buf = torch.empty(n + 256, dtype=torch.uint8, device=device or U.device)
+        ptr = (self.buf.data_ptr() + 255) & ~255
+        h = C.c_void_p()
+        _check(lib().pcas_solver_create(C.byref(h), _dev(f0, "f0", N, dt), _dev(mean, "mean", 3 * N, dt),
+                                        _dev(U, "U", None, dt), storage_type(U), self.K, C.byref(self.vol),
+                                        C.byref(self.cb), C.byref(params_struct(params)), ptr, n,
+                                        _stream(stream)))
+        self.h = h
+
+    def y_buffer(self):
+        """Device address of the solver's own image buffer (nu * nv float32)."""
+        return lib().pcas_solver_y_buffer(self.h)
+
+    def solve(self, y, w_init, angle=None, off_u=None, off_v=None, stream=None):
+        """Returns (w (K,), stats dict).  y: CUDA float32 tensor or None (use y_buffer())."""
+        nu, nv = self.cb.nu, self.cb.nv
+        w0 = _host_d(w_init, self.K)
+        w_out = np.zeros(self.K)
+        st = Stats()
+        _check(lib().pcas_solver_solve(self.h, None if y is None else _dev(y, "y", nu * nv),
+                                       float(self.cb.angle_rad if angle is None else angle),
+                                       float(self.cb.off_u if off_u is None else off_u),
+                                       float(self.cb.off_v if off_v is None else off_v),
+                                       w0.ctypes.data_as(_D), w_out.ctypes.data_as(_D), C.byref(st),
+                                       _stream(stream)))
+        return w_out, {k: getattr(st, k) for k, _ in Stats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pcas_solver_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many device-driven solves (uneven sizes) as branches of one CUDA graph:
+    one launch solves them all.  ys[i]: CUDA tensor copied into solver i's image
+    buffer at each launch (or None)."""
+
+    def __init__(self, solvers, ys=None, stream=None):
+        self.solvers = list(solvers)
+        n = len(self.solvers)
+        arr = (C.c_void_p * n)(*[s.h.value for s in self.solvers])
+        ysrc = None
+        if ys is not None:
+            self.ys = list(ys)
+            ysrc = (C.c_void_p * n)(*[None if y is None else _dev(y, "y") for y in self.ys])
+        h = C.c_void_p()
+        _check(lib().pcas_batch_create(C.byref(h), arr, ysrc, n, _stream(stream)))
+        self.h = h
+
+    def solve(self, angles, w_init, stream=None):
+        """angles (n,), w_init list of n K_i-vectors -> (list of w, list of stats dicts)."""
+        n = len(self.solvers)
+        W0 = np.zeros((n, KMAX))
+        for i, w in enumerate(w_init):
+            W0[i, :len(w)] = w
+        ang = _host_d(angles, n)
+        Wout = np.zeros((n, KMAX))
+        st = (Stats * n)()
+        _check(lib().pcas_batch_solve(self.h, ang.ctypes.data_as(_D), W0.ctypes.data_as(_D),
+                                      Wout.ctypes.data_as(_D), st, _stream(stream)))
+        return ([Wout[i, :s.K].copy() for i, s in enumerate(self.solvers)],
+                [{k: getattr(st[i], k) for k, _ in Stats._fields_} for i in range(n)])
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pcas_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def profile(on: bool):
