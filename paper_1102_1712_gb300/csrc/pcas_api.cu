@@ -141,6 +141,7 @@ int make_view(const pcas_vol* vol, const pcas_cb* cb, double step, View* V) {
     V->nu = cb->nu;
     V->nv = cb->nv;
     V->step = (float)step;
+    V->xy_swap = fabs(sa) > fabs(ca) ? 1 : 0;
     return PCAS_OK;
 }
 
@@ -159,8 +160,10 @@ struct Layout {
 
 Layout layout(const pcas_vol* vol, const pcas_cb* cb, int K) {
     Layout L;
-    Pad pd = make_pad(vol->nx, vol->ny, vol->nz);
-    const size_t npad = (size_t)pd.px * pd.pny * pd.pnz;
+    // room for either solver layout (x fastest or y fastest)
+    const Pad pa = solver_pad(vol->nx, vol->ny, vol->nz, 0), pb = solver_pad(vol->nx, vol->ny, vol->nz, 1);
+    const size_t na = (size_t)pa.px * pa.pny * pa.pnz, nb = (size_t)pb.px * pb.pny * pb.pnz;
+    const size_t npad = na > nb ? na : nb;
     size_t M = (size_t)cb->nu * cb->nv;
     size_t off = 0;
     L.state = off; off += align256(sizeof(SolveState));
@@ -352,14 +355,14 @@ int check_finite(const double* v, int n, const char* name) {
 // Everything up to and including the gradient at st->w: warp, DRR with
 // moments, (A.1) + residual + J, fused adjoint gradient.
 int eval_gradient_pipeline(const void* f0, const void* mean, const void* U, int dt, int K, const float* y,
-                           const Grid& g, const Pad& pd, const View& V, const Ws& W, int step_setup,
+                           const Grid& g, const View& V, const Ws& W, int step_setup,
                            cudaStream_t s) {
     WSrc ws{};
     ws.dev = W.st->w;
     ws.phase = &W.st->phase;
-    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, dt, K, ws, g, pd, W.fpad, W.st->box[0], s));
+    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, dt, K, ws, g, W.view, W.fpad, W.st->box[0], s));
     PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
-                launch_drr_solver(W.fpad, W.fpad4, g, pd, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, s));
+                launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, s));
     PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, W.view, 1, W.rayt, W.st, W.part_res, s));
     PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
                 launch_adjoint_grad(W.rayt, g, W.view, f0, mean, U, dt, K, step_setup, W.st, W.part_adj, W.adj,
@@ -484,11 +487,10 @@ int cost_grad_typed(const void* f0, const void* mean, const void* U, int dtype, 
     PCAS_TRY(bind_ws(ws, ws_bytes, vol, cb, K, &W));
     cudaStream_t s = as_stream(stream);
     Grid g = make_grid(vol);
-    Pad pd = make_pad(vol->nx, vol->ny, vol->nz);
     PCAS_CUDA(cudaMemsetAsync(W.fpad, 0, W.fpad_bytes, s));
     PCAS_TRY(launch_init(W.st, K, w, nullptr, s));
     PCAS_TRY(upload_view(W.view, V, s));
-    PCAS_TRY(eval_gradient_pipeline(f0, mean, U, dtype, K, y, g, pd, V, W, 0, s));
+    PCAS_TRY(eval_gradient_pipeline(f0, mean, U, dtype, K, y, g, V, W, 0, s));
     SolveState h;
     PCAS_CUDA(cudaMemcpyAsync(&h, W.st, sizeof(h), cudaMemcpyDeviceToHost, s));
     PCAS_CUDA(cudaStreamSynchronize(s));
@@ -539,16 +541,15 @@ int cost_grad_f0(const float* f0, const float* mean, const float* U, int K, cons
     unsigned int* zmax = reinterpret_cast<unsigned int*>(extra + align256(N * sizeof(float)) + align256(N * 8));
     cudaStream_t s = as_stream(stream);
     Grid g = make_grid(vol);
-    Pad pd = make_pad(vol->nx, vol->ny, vol->nz);
     PCAS_CUDA(cudaMemsetAsync(W.fpad, 0, W.fpad_bytes, s));
     PCAS_TRY(launch_init(W.st, K, w, nullptr, s));
     PCAS_TRY(upload_view(W.view, V, s));
     WSrc wsrc{};
     wsrc.dev = W.st->w;
     wsrc.phase = &W.st->phase;
-    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, DT_F32, K, wsrc, g, pd, W.fpad, W.st->box[0], s));
+    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, DT_F32, K, wsrc, g, W.view, W.fpad, W.st->box[0], s));
     PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
-                launch_drr_solver(W.fpad, W.fpad4, g, pd, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, s));
+                launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, s));
     PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, W.view, 1, W.rayt, W.st, W.part_res, s));
     if (dJdw)
         PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
@@ -590,7 +591,6 @@ int solve_projection_typed(const void* f0, const void* mean, const void* U, int 
     PCAS_TRY(bind_ws(ws, ws_bytes, vol, cb, K, &W));
     cudaStream_t s = as_stream(stream);
     Grid g = make_grid(vol);
-    Pad pd = make_pad(vol->nx, vol->ny, vol->nz);
     const int adj_cap = adjoint_block_cap();
     PCAS_CUDA(cudaMemsetAsync(W.fpad, 0, W.fpad_bytes + W.fpad4_bytes, s));   // zero halos
     PCAS_TRY(launch_init(W.st, K, w_init, prm, s));
@@ -601,9 +601,9 @@ int solve_projection_typed(const void* f0, const void* mean, const void* U, int 
     wtrial.dev = W.st->wt[0];
     wtrial.phase = &W.st->phase;
     wtrial.nvalid = &W.st->nvalid;
-    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, dtype, K, wcur, g, pd, W.fpad, W.st->box[0], s));
+    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, dtype, K, wcur, g, W.view, W.fpad, W.st->box[0], s));
     PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
-                launch_drr_solver(W.fpad, W.fpad4, g, pd, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, s));
+                launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, s));
     int iters = 0, phase = PH_RUNNING;
     for (int it = 0; it < prm->max_iter; it++) {
         PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, W.view, it == 0, W.rayt, W.st, W.part_res, s));
@@ -631,14 +631,14 @@ int solve_projection_typed(const void* f0, const void* mean, const void* U, int 
                 break;
             }
             if (nvalid >= 2) {
-                PCAS_LAUNCH(PCAS_K_WARP_BATCH, s, launch_warp_batch(f0, mean, U, dtype, K, W.st, g, pd, W.fpad4, s));
+                PCAS_LAUNCH(PCAS_K_WARP_BATCH, s, launch_warp_batch(f0, mean, U, dtype, K, W.st, g, W.view, W.fpad4, s));
                 PCAS_LAUNCH(PCAS_K_DRR_BATCH, s,
-                            launch_drr_solver(W.fpad, W.fpad4, g, pd, V, W.view, y, W.pbuf, TRIAL_BATCH,
+                            launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, TRIAL_BATCH,
                                               W.st, W.part_drr, s));
             } else {
-                PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, dtype, K, wtrial, g, pd, W.fpad, W.st->box[0], s));
+                PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, dtype, K, wtrial, g, W.view, W.fpad, W.st->box[0], s));
                 PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
-                            launch_drr_solver(W.fpad, W.fpad4, g, pd, V, W.view, y, W.pbuf, 1, W.st, W.part_drr, s));
+                            launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 1, W.st, W.part_drr, s));
             }
             PCAS_CUDA(cudaMemcpyAsync(&phase, &W.st->phase, sizeof(int), cudaMemcpyDeviceToHost, s));
             PCAS_CUDA(cudaStreamSynchronize(s));
@@ -950,6 +950,7 @@ struct pcas_solver_s {
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     View view0;           // geometry at creation (grid sizes)
+    int layout;           // xy_swap of the last staged view; -1: buffers all zero
 };
 
 struct pcas_batch_s {
@@ -968,7 +969,6 @@ size_t solver_extra(const pcas_cb* cb) {
 // (optionally preceded by a copy of the measured image from y_src).
 int capture_solve(pcas_solver s, cudaGraph_t graph, cudaStream_t cs, const float* y_src) {
     const Grid g = make_grid(&s->vol);
-    const Pad pd = make_pad(s->vol.nx, s->vol.ny, s->vol.nz);
     const Ws& W = s->W;
     const View& V = s->view0;
     const size_t M = (size_t)s->cb.nu * s->cb.nv;
@@ -986,8 +986,8 @@ int capture_solve(pcas_solver s, cudaGraph_t graph, cudaStream_t cs, const float
     WSrc wtrial = wcur;
     wtrial.dev = W.st->wt[0];
     wtrial.nvalid = &W.st->nvalid;
-    PCAS_G(launch_warp_pca(s->f0, s->mean, s->U, s->dtype, s->K, wcur, g, pd, W.fpad, W.st->box[0], cs));
-    PCAS_G(launch_drr_solver(W.fpad, W.fpad4, g, pd, V, W.view, s->y, W.pbuf, 0, W.st, W.part_drr, cs));
+    PCAS_G(launch_warp_pca(s->f0, s->mean, s->U, s->dtype, s->K, wcur, g, W.view, W.fpad, W.st->box[0], cs));
+    PCAS_G(launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, s->y, W.pbuf, 0, W.st, W.part_drr, cs));
     k_ctrl_start<<<1, 1, 0, cs>>>(W.st, s->h_outer);
     PCAS_G(cudaGetLastError());
     cudaGraph_t outer_body;
@@ -1009,10 +1009,10 @@ int capture_solve(pcas_solver s, cudaGraph_t graph, cudaStream_t cs, const float
     PCAS_G(cudaStreamEndCapture(cs, &done));
     // one candidate batch: the four-volume pair or the one-volume pair runs
     PCAS_G(cudaStreamBeginCaptureToGraph(cs, inner_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    PCAS_G(launch_warp_batch(s->f0, s->mean, s->U, s->dtype, s->K, W.st, g, pd, W.fpad4, cs));
-    PCAS_G(launch_drr_solver(W.fpad, W.fpad4, g, pd, V, W.view, s->y, W.pbuf, TRIAL_BATCH, W.st, W.part_drr, cs));
-    PCAS_G(launch_warp_pca(s->f0, s->mean, s->U, s->dtype, s->K, wtrial, g, pd, W.fpad, W.st->box[0], cs));
-    PCAS_G(launch_drr_solver(W.fpad, W.fpad4, g, pd, V, W.view, s->y, W.pbuf, 1, W.st, W.part_drr, cs));
+    PCAS_G(launch_warp_batch(s->f0, s->mean, s->U, s->dtype, s->K, W.st, g, W.view, W.fpad4, cs));
+    PCAS_G(launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, s->y, W.pbuf, TRIAL_BATCH, W.st, W.part_drr, cs));
+    PCAS_G(launch_warp_pca(s->f0, s->mean, s->U, s->dtype, s->K, wtrial, g, W.view, W.fpad, W.st->box[0], cs));
+    PCAS_G(launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, s->y, W.pbuf, 1, W.st, W.part_drr, cs));
     k_ctrl_batch_end<<<1, 1, 0, cs>>>(W.st, s->h_inner);
     PCAS_G(cudaGetLastError());
     PCAS_G(cudaStreamEndCapture(cs, &done));
@@ -1021,7 +1021,8 @@ int capture_solve(pcas_solver s, cudaGraph_t graph, cudaStream_t cs, const float
 
 #undef PCAS_G
 
-int solver_stage(pcas_solver s, double angle_rad, double off_u, double off_v, const double* w_init) {
+int solver_stage(pcas_solver s, double angle_rad, double off_u, double off_v, const double* w_init,
+                 cudaStream_t st) {
     pcas_cb cb = s->cb;
     cb.angle_rad = angle_rad;
     cb.off_u = off_u;
@@ -1029,6 +1030,9 @@ int solver_stage(pcas_solver s, double angle_rad, double off_u, double off_v, co
     View V;
     PCAS_TRY(make_view(&s->vol, &cb, s->prm.step_mm, &V));
     PCAS_TRY(check_finite(w_init, s->K, "w_init"));
+    if (s->layout >= 0 && s->layout != V.xy_swap)   // the other layout's voxels lie on this one's halo
+        PCAS_CUDA(cudaMemsetAsync(s->W.fpad, 0, s->W.fpad_bytes + s->W.fpad4_bytes, st));
+    s->layout = V.xy_swap;
     *s->h_view = V;
     InitBlock ib = {};
     for (int k = 0; k < s->K; k++) ib.w[k] = w_init[k];
@@ -1096,7 +1100,7 @@ int pcas_solver_create(pcas_solver* out, const void* f0, const void* mean, const
     const size_t base = layout(vol, cb, K).total;
     pcas_solver s = new pcas_solver_s();
     s->vol = *vol; s->cb = *cb; s->prm = *prm; s->K = K; s->dtype = dtype;
-    s->f0 = f0; s->mean = mean; s->U = U; s->view0 = V;
+    s->f0 = f0; s->mean = mean; s->U = U; s->view0 = V; s->layout = -1;
     int rc = bind_ws(ws, base, vol, cb, K, &s->W);
     if (rc != PCAS_OK) { solver_free(s); return rc; }
     char* extra = static_cast<char*>(ws) + base;
@@ -1137,8 +1141,8 @@ int pcas_solver_solve(pcas_solver s, const float* y, double angle_rad, double of
                       const double* w_init, double* w_out, pcas_stats* stats, void* stream) {
     PCAS_TRY(check_ptr(s, "solver"));
     PCAS_TRY(check_ptr(w_init, "w_init"));
-    PCAS_TRY(solver_stage(s, angle_rad, off_u, off_v, w_init));
     cudaStream_t st = as_stream(stream);
+    PCAS_TRY(solver_stage(s, angle_rad, off_u, off_v, w_init, st));
     const size_t M = (size_t)s->cb.nu * s->cb.nv;
     if (y && y != s->y) PCAS_CUDA(cudaMemcpyAsync(s->y, y, M * sizeof(float), cudaMemcpyDeviceToDevice, st));
     PCAS_CUDA(cudaGraphLaunch(s->exec, st));
@@ -1198,10 +1202,10 @@ int pcas_batch_solve(pcas_batch b, const double* angle_rad, const double* w_init
     PCAS_TRY(check_ptr(angle_rad, "angle_rad"));
     PCAS_TRY(check_ptr(w_init, "w_init"));
     const int n = (int)b->solvers.size();
+    cudaStream_t st = as_stream(stream);
     for (int i = 0; i < n; i++)
         PCAS_TRY(solver_stage(b->solvers[i], angle_rad[i], b->solvers[i]->cb.off_u, b->solvers[i]->cb.off_v,
-                              w_init + (size_t)i * PCAS_KMAX));
-    cudaStream_t st = as_stream(stream);
+                              w_init + (size_t)i * PCAS_KMAX, st));
     PCAS_CUDA(cudaGraphLaunch(b->exec, st));
     for (int i = 0; i < n; i++)
         PCAS_CUDA(cudaMemcpyAsync(b->solvers[i]->h_state, b->solvers[i]->W.st, sizeof(SolveState),

@@ -24,6 +24,7 @@ struct View {
     float u0, du, v0, dv;    // detector coordinates of pixel centres, mm
     int nu, nv;
     float step;              // ray-march step, mm
+    int xy_swap;             // solver volumes stored with x and y exchanged (|sin a| > |cos a|)
 };
 
 struct Grid {
@@ -50,6 +51,17 @@ __host__ __device__ inline Pad make_pad(int nx, int ny, int nz) {
 
 __host__ __device__ inline long pad_index(const Pad& pd, int i, int j, int k) {
     return ((long)(k + 2) * pd.pny + (j + 2)) * pd.px + (i + 4);
+}
+
+// Solver volume layout.  A ray crosses voxels mostly along its dominant
+// direction, and a warp's rays are neighbours along the detector u axis,
+// which is world x at gantry 0 and world y at 90 degrees.  For views with
+// |sin a| > |cos a| the warp kernels store the solver volumes with x and y
+// exchanged (y fastest), so that u-neighbouring rays read neighbouring
+// addresses at every angle; the projector then marches the mirrored
+// geometry: the same sample points with their x and y coordinates exchanged.
+__host__ __device__ inline Pad solver_pad(int nx, int ny, int nz, int xy_swap) {
+    return xy_swap ? make_pad(ny, nx, nz) : make_pad(nx, ny, nz);
 }
 
 // Trial step sizes evaluated together in one warp + projection pass.
@@ -227,6 +239,20 @@ __device__ __forceinline__ float4 tri_padded4(const float4* __restrict__ f, cons
 }
 
 // ----------------------------------------------------------------- rays
+template <typename X>
+__device__ __forceinline__ void swap_xy(X& a, X& b) { X t = a; a = b; b = t; }
+
+// The view, grid and layout of the solver volumes in the frame they are stored
+// in (see solver_pad): a no-op unless V.xy_swap is set.
+__device__ __forceinline__ void solver_frame(View& V, Grid& g, Pad& pd) {
+    if (V.xy_swap) {
+        swap_xy(V.Q0.x, V.Q0.y); swap_xy(V.A.x, V.A.y); swap_xy(V.Bu.x, V.Bu.y); swap_xy(V.Bv.x, V.Bv.y);
+        swap_xy(V.EW.x, V.EW.y); swap_xy(V.EU.x, V.EU.y); swap_xy(V.EV.x, V.EV.y);
+        swap_xy(g.nx, g.ny); swap_xy(g.inv_sx, g.inv_sy);
+    }
+    pd = make_pad(g.nx, g.ny, g.nz);
+}
+
 // Unit ray direction of pixel (iu, iv) in voxel units per mm.
 __device__ __forceinline__ float3 ray_dir(const View& V, int iu, int iv) {
     float u = fmaf((float)iu, V.du, V.u0), v = fmaf((float)iv, V.dv, V.v0);
@@ -355,16 +381,18 @@ cudaError_t launch_pca_dvf(const void* mean, const void* U, int dt, int K, const
 cudaError_t launch_warp_dvf(const void* f0, int dt, const float* dvf, Grid g, float* f, cudaStream_t s);
 // Solver warp: S = 1 writes f(w_src) to the scalar zero-halo buffer; S = 4
 // writes the four candidate volumes st->wt[0..3] interleaved (float4).
+// Vd (device, may be null): its xy_swap selects the layout (solver_pad); the
+// bounding box is recorded in the same frame.
 cudaError_t launch_warp_pca(const void* f0, const void* mean, const void* U, int dt, int K, WSrc w,
-                            Grid g, Pad pd, float* fpad, int* box, cudaStream_t s);
+                            Grid g, const View* Vd, float* fpad, int* box, cudaStream_t s);
 cudaError_t launch_warp_batch(const void* f0, const void* mean, const void* U, int dt, int K,
-                              const SolveState* st, Grid g, Pad pd, float4* fpad4, cudaStream_t s);
+                              const SolveState* st, Grid g, const View* Vd, float4* fpad4, cudaStream_t s);
 cudaError_t launch_drr_plain(const float* f, Grid g, const View& V, float* p, cudaStream_t s);
 // Solver projector.  mode 0: first evaluation into buffer cur; mode 1: one
 // trial volume; mode 4: the four-volume batch (st->nvalid of them on the
 // schedule).  Vh: the view on the host (grid size), Vd: the same in device
 // memory (read by the kernels, so captured launches stay view-independent).
-cudaError_t launch_drr_solver(const float* fpad, const float4* fpad4, Grid g, Pad pd,
+cudaError_t launch_drr_solver(const float* fpad, const float4* fpad4, Grid g,
                               const View& Vh, const View* Vd, const float* y, float* pbuf, int mode,
                               SolveState* st, double* part, cudaStream_t s);
 cudaError_t launch_resid(const float* pbuf, const float* y, const View& Vh, const View* Vd, int first,

@@ -100,10 +100,12 @@ k_warp_dvf(const T* __restrict__ f0, const float* __restrict__ dvf, Grid g, long
 template <bool VEC, typename T>
 __global__ void __launch_bounds__(kWarpThreads)
 k_warp_pca(const T* __restrict__ f0, const T* __restrict__ mean,
-           const T* __restrict__ U, int K, WSrc ws, Grid g, Pad pd, long N,
+           const T* __restrict__ U, int K, WSrc ws, Grid g, const View* __restrict__ Vp, long N,
            float* __restrict__ fpad, int* __restrict__ box_out) {
     if (ws.phase && *ws.phase >= PH_STOP) return;
     if (ws.nvalid && *ws.nvalid != 1) return;
+    const int swp = Vp ? Vp->xy_swap : 0;
+    const Pad pd = solver_pad(g.nx, g.ny, g.nz, swp);
     __shared__ float s_w[PCAS_KMAX];
     if (threadIdx.x < PCAS_KMAX)
         s_w[threadIdx.x] = ws.dev ? (threadIdx.x < K ? (float)ws.dev[threadIdx.x] : 0.f)
@@ -124,9 +126,17 @@ k_warp_pca(const T* __restrict__ f0, const T* __restrict__ mean,
             for (int e = 0; e < 4; e++) {
                 o[e] = tri_dense(f0, g, fmaf(x[0][e], g.inv_sx, (float)(i + e)),
                                  fmaf(x[1][e], g.inv_sy, (float)j), fmaf(x[2][e], g.inv_sz, (float)k));
-                if (o[e] != 0.0f) box_add(b, i + e, j, k);
+                if (o[e] != 0.0f) {
+                    if (swp) box_add(b, j, i + e, k);
+                    else box_add(b, i + e, j, k);
+                }
             }
-            *reinterpret_cast<float4*>(fpad + pad_index(pd, i, j, k)) = make_float4(o[0], o[1], o[2], o[3]);
+            if (swp) {
+#pragma unroll
+                for (int e = 0; e < 4; e++) fpad[pad_index(pd, j, i + e, k)] = o[e];
+            } else {
+                *reinterpret_cast<float4*>(fpad + pad_index(pd, i, j, k)) = make_float4(o[0], o[1], o[2], o[3]);
+            }
         }
     } else if (t < N) {
         int i = (int)(t % g.nx);
@@ -140,8 +150,13 @@ k_warp_pca(const T* __restrict__ f0, const T* __restrict__ mean,
         }
         const float o = tri_dense(f0, g, fmaf(x[0], g.inv_sx, (float)i), fmaf(x[1], g.inv_sy, (float)j),
                                   fmaf(x[2], g.inv_sz, (float)k));
-        if (o != 0.0f) box_add(b, i, j, k);
-        fpad[pad_index(pd, i, j, k)] = o;
+        if (swp) {
+            if (o != 0.0f) box_add(b, j, i, k);
+            fpad[pad_index(pd, j, i, k)] = o;
+        } else {
+            if (o != 0.0f) box_add(b, i, j, k);
+            fpad[pad_index(pd, i, j, k)] = o;
+        }
     }
     box_reduce(b, box_out);
 }
@@ -154,9 +169,11 @@ k_warp_pca(const T* __restrict__ f0, const T* __restrict__ mean,
 template <typename T>
 __global__ void __launch_bounds__(kWarpThreads)
 k_warp_batch(const T* __restrict__ f0, const T* __restrict__ mean,
-             const T* __restrict__ U, int K, const SolveState* st, Grid g, Pad pd, long N,
-             float4* __restrict__ fpad4, int* __restrict__ box_out) {
+             const T* __restrict__ U, int K, const SolveState* st, Grid g, const View* __restrict__ Vp,
+             long N, float4* __restrict__ fpad4, int* __restrict__ box_out) {
     if (st->phase >= PH_STOP || st->nvalid < 2) return;
+    const int swp = Vp ? Vp->xy_swap : 0;
+    const Pad pd = solver_pad(g.nx, g.ny, g.nz, swp);
     __shared__ float s_w[TRIAL_BATCH][PCAS_KMAX];
     if (threadIdx.x < TRIAL_BATCH * PCAS_KMAX) {
         const int j = threadIdx.x / PCAS_KMAX, k = threadIdx.x % PCAS_KMAX;
@@ -189,8 +206,9 @@ k_warp_batch(const T* __restrict__ f0, const T* __restrict__ mean,
         for (int b = 0; b < TRIAL_BATCH; b++)
             o[b] = tri_dense(f0, g, fmaf(x[b][0], g.inv_sx, (float)i), fmaf(x[b][1], g.inv_sy, (float)j),
                              fmaf(x[b][2], g.inv_sz, (float)k));
-        fpad4[pad_index(pd, i, j, k)] = make_float4(o[0], o[1], o[2], o[3]);
-        if (o[0] != 0.0f || o[1] != 0.0f || o[2] != 0.0f || o[3] != 0.0f) box_add(bx, i, j, k);
+        const int a0 = swp ? j : i, a1 = swp ? i : j;
+        fpad4[pad_index(pd, a0, a1, k)] = make_float4(o[0], o[1], o[2], o[3]);
+        if (o[0] != 0.0f || o[1] != 0.0f || o[2] != 0.0f || o[3] != 0.0f) box_add(bx, a0, a1, k);
     }
     box_reduce(bx, box_out);      // every thread of the block, one call site
 }
@@ -215,16 +233,16 @@ cudaError_t pca_dvf_t(const void* mean, const void* U, int K, const float* w, Gr
 }
 
 template <typename T>
-cudaError_t warp_pca_t(const void* f0, const void* mean, const void* U, int K, WSrc w, Grid g, Pad pd,
-                       float* fpad, int* box, cudaStream_t s) {
+cudaError_t warp_pca_t(const void* f0, const void* mean, const void* U, int K, WSrc w, Grid g,
+                       const View* Vd, float* fpad, int* box, cudaStream_t s) {
     long N = (long)g.nx * g.ny * g.nz;
     const unsigned a = sizeof(T) * 4;
     bool vec = (g.nx % 4 == 0) && aligned(mean, a) && aligned(U, a) && aligned(fpad, 16);
     const T* f = static_cast<const T*>(f0);
     const T* m = static_cast<const T*>(mean);
     const T* u = static_cast<const T*>(U);
-    if (vec) k_warp_pca<true, T><<<blocks_for(N / 4), kWarpThreads, 0, s>>>(f, m, u, K, w, g, pd, N, fpad, box);
-    else k_warp_pca<false, T><<<blocks_for(N), kWarpThreads, 0, s>>>(f, m, u, K, w, g, pd, N, fpad, box);
+    if (vec) k_warp_pca<true, T><<<blocks_for(N / 4), kWarpThreads, 0, s>>>(f, m, u, K, w, g, Vd, N, fpad, box);
+    else k_warp_pca<false, T><<<blocks_for(N), kWarpThreads, 0, s>>>(f, m, u, K, w, g, Vd, N, fpad, box);
     return cudaGetLastError();
 }
 
@@ -251,17 +269,17 @@ cudaError_t launch_warp_dvf(const void* f0, int dt, const float* dvf, Grid g, fl
 }
 
 cudaError_t launch_warp_pca(const void* f0, const void* mean, const void* U, int dt, int K, WSrc w,
-                            Grid g, Pad pd, float* fpad, int* box, cudaStream_t s) {
-    PCAS_DT_DISPATCH(dt, (warp_pca_t<T>(f0, mean, U, K, w, g, pd, fpad, box, s)))
+                            Grid g, const View* Vd, float* fpad, int* box, cudaStream_t s) {
+    PCAS_DT_DISPATCH(dt, (warp_pca_t<T>(f0, mean, U, K, w, g, Vd, fpad, box, s)))
 }
 
 cudaError_t launch_warp_batch(const void* f0, const void* mean, const void* U, int dt, int K,
-                              const SolveState* st, Grid g, Pad pd, float4* fpad4, cudaStream_t s) {
+                              const SolveState* st, Grid g, const View* Vd, float4* fpad4, cudaStream_t s) {
     long N = (long)g.nx * g.ny * g.nz;
     int* box = const_cast<int*>(st->box[1]);
     PCAS_DT_DISPATCH(dt, (k_warp_batch<T><<<blocks_for(N), kWarpThreads, 0, s>>>(
                               static_cast<const T*>(f0), static_cast<const T*>(mean),
-                              static_cast<const T*>(U), K, st, g, pd, N, fpad4, box),
+                              static_cast<const T*>(U), K, st, g, Vd, N, fpad4, box),
                           cudaGetLastError()))
 }
 

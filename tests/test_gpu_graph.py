@@ -101,3 +101,30 @@ def test_batch_of_uneven_solves(P):
     batch.close()
     for sv in solvers:
         sv.close()
+
+
+def test_layout_follows_the_angle(P):
+    """Views with |sin a| > |cos a| keep the solver volumes y-fastest.  One
+    solver (x != y grid) walks through angles on both sides of every 45-degree
+    boundary and back: each result equals the host-driven solve bitwise and the
+    oracle's cost and gradient within the parity tolerances."""
+    dims = (61, 47, 29, 4.0, 3.5, 4.5)
+    w_true = np.array([0.6, -0.3, 0.4])
+    pb = make_problem(dims, 3, (101, 77, 3.5, 3.5), 0.0, w_true, noise=0.0, seeds=(91, 92, 93))
+    d = to_dev(pb)
+    prm = P.default_params(pb["step"])
+    sv = P.Solver(d["f0"], None, d["U"], pb["vol"], pb["cb"], prm)
+    w_eval = 0.7 * w_true
+    for ang in (0.3, 0.9, 2.0, 2.5, 3.3, 4.4, 5.0, 0.1, np.pi / 4 + 1e-3, np.pi / 4 - 1e-3):
+        cb = dict(pb["cb"], angle=float(ang))
+        y = O.drr_forward(O.warp_volume(pb["f0"], O.pca_dvf(None, pb["U"], w_true, pb["vol"]), pb["vol"]),
+                          pb["vol"], cb, pb["step"]).astype(np.float32)
+        yd = torch.from_numpy(y).cuda()
+        w_g, st_g = sv.solve(yd, np.zeros(3), angle=ang)
+        w_h, st_h = P.solve_projection(d["f0"], None, d["U"], yd, pb["vol"], cb, np.zeros(3), prm)
+        assert np.array_equal(w_g, w_h) and st_g == st_h, ang
+        J, G, _ = P.cost_grad(d["f0"], None, d["U"], w_eval, yd, pb["vol"], cb, pb["step"])
+        Jo, Go, _ = O.cost_grad(pb["f0"], None, pb["U"], w_eval, y, pb["vol"], cb, pb["step"])
+        assert abs(J - Jo) <= 1e-4 * Jo, (ang, J, Jo)
+        assert np.linalg.norm(G - Go) <= 1e-3 * np.linalg.norm(Go), (ang, G, Go)
+    sv.close()
