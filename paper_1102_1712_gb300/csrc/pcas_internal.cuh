@@ -313,11 +313,11 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 // FP64 across warps.  Writes this block's NV doubles to red.part[blk * NV + j]
 // and returns true in every thread of the block that finished last; that
 // block's thread j < NV then holds the fixed-order FP64 total in out[j]
-// (shared memory).  blockDim.x must be a multiple of 32, at most 1024.
-template <int NV>
+// (shared memory).  blockDim.x must be a multiple of 32, at most 32 NW.
+template <int NV, int NW = 32>
 __device__ bool block_reduce_last(const float (&v)[NV], Reduce red, unsigned int nblocks,
                                   unsigned int blk, double* out /* shared, NV */) {
-    __shared__ double s_w[32][NV];
+    __shared__ double s_w[NW][NV];      // per-warp sums; reused for the final tree
     __shared__ bool s_last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
@@ -341,7 +341,7 @@ __device__ bool block_reduce_last(const float (&v)[NV], Reduce red, unsigned int
     if (!s_last) return false;
     __threadfence();
     // fixed-order reduction: thread t sums blocks t, t+nt, ...; then a tree
-    __shared__ double s_acc[1024 / 32][NV];
+    double(&s_acc)[NW][NV] = s_w;      // free again: read before the barriers above
     double acc[NV];
 #pragma unroll
     for (int j = 0; j < NV; j++) acc[j] = 0.0;
