@@ -80,8 +80,12 @@ int check_vol(const pcas_vol* v) {
     if (!v) return fail(PCAS_ERR_INVALID_ARG, "vol is NULL");
     if (v->nx < 1 || v->ny < 1 || v->nz < 1)
         return fail(PCAS_ERR_INVALID_ARG, "volume dims must be positive (%d,%d,%d)", v->nx, v->ny, v->nz);
-    if ((double)v->nx * v->ny * v->nz > 2.0e9)
-        return fail(PCAS_ERR_INVALID_ARG, "volume has more than 2e9 voxels");
+    // 32-bit voxel offsets: either zero-halo layout (at most (m + 10) (m + 4) (nz + 4)
+    // elements, m = max(nx, ny)) stays below 2^31; ny, nz index grid rows
+    const double m = v->nx > v->ny ? v->nx : v->ny;
+    if ((m + 10.0) * (m + 4.0) * (v->nz + 4.0) > 2147483647.0 || v->ny > 65535 || v->nz > 65535)
+        return fail(PCAS_ERR_INVALID_ARG, "volume too large (%d,%d,%d): at most 2^31 voxels with halo, "
+                    "ny and nz at most 65535", v->nx, v->ny, v->nz);
     if (!(v->sx > 0) || !(v->sy > 0) || !(v->sz > 0))
         return fail(PCAS_ERR_INVALID_ARG, "voxel spacing must be positive");
     if (!isfinite(v->ox) || !isfinite(v->oy) || !isfinite(v->oz))

@@ -169,7 +169,7 @@ __device__ __forceinline__ float tri_dense(const T* __restrict__ f, const Grid& 
     float fx = floorf(qx), fy = floorf(qy), fz = floorf(qz);
     int lx = (int)fx, ly = (int)fy, lz = (int)fz;
     float zx = qx - fx, zy = qy - fy, zz = qz - fz;
-    const long sy = g.nx, sz = (long)g.nx * g.ny;
+    const int sy = g.nx, sz = g.nx * g.ny;    // 32-bit offsets: volumes have < 2^31 voxels
     float v000, v100, v010, v110, v001, v101, v011, v111;
     if (lx >= 0 && ly >= 0 && lz >= 0 && lx < g.nx - 1 && ly < g.ny - 1 && lz < g.nz - 1) {
         const T* b = f + lz * sz + ly * sy + lx;

@@ -45,7 +45,7 @@ __device__ __forceinline__ void box_reduce(int b[6], int* __restrict__ out) {
     __syncthreads();
     if (threadIdx.x < 6) {
         int m = BOX_EMPTY;
-        for (int w = 0; w < kWarpThreads / 32; w++) m = min(m, s_b[w][threadIdx.x]);
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) m = min(m, s_b[w][threadIdx.x]);
         if (m != BOX_EMPTY) atomicMin(out + threadIdx.x, m);
     }
 }
@@ -95,30 +95,38 @@ k_warp_dvf(const T* __restrict__ f0, const float* __restrict__ dvf, Grid g, long
     f[n] = tri_dense(f0, g, qx, qy, qz);
 }
 
+// Thread layout of the solver warps: blockIdx.z = k, blockIdx.y = j and
+// i = (blockIdx.x blockDim.x + threadIdx.x) V with V voxels per thread (no
+// index divisions; 32-bit voxel offsets, volumes have < 2^31 voxels).
+
 // Fused DVF synthesis + warp into the zero-halo layout used by the solver.
 // VEC: 4 voxels per thread along x (nx % 4 == 0, 16-byte aligned model).
 template <bool VEC, typename T>
 __global__ void __launch_bounds__(kWarpThreads)
 k_warp_pca(const T* __restrict__ f0, const T* __restrict__ mean,
-           const T* __restrict__ U, int K, WSrc ws, Grid g, const View* __restrict__ Vp, long N,
+           const T* __restrict__ U, int K, WSrc ws, Grid g, const View* __restrict__ Vp,
            float* __restrict__ fpad, int* __restrict__ box_out) {
     if (ws.phase && *ws.phase >= PH_STOP) return;
     if (ws.nvalid && *ws.nvalid != 1) return;
     const int swp = Vp ? Vp->xy_swap : 0;
     const Pad pd = solver_pad(g.nx, g.ny, g.nz, swp);
     __shared__ float s_w[PCAS_KMAX];
-    if (threadIdx.x < PCAS_KMAX)
-        s_w[threadIdx.x] = ws.dev ? (threadIdx.x < K ? (float)ws.dev[threadIdx.x] : 0.f)
-                                  : ws.w[threadIdx.x];
+    if (threadIdx.x < PCAS_KMAX) {
+        float wv = 0.f;                     // static indices keep ws out of local memory
+#pragma unroll
+        for (int t = 0; t < PCAS_KMAX; t++)
+            if (threadIdx.x == t) wv = ws.w[t];
+        s_w[threadIdx.x] = ws.dev ? (threadIdx.x < K ? (float)ws.dev[threadIdx.x] : 0.f) : wv;
+    }
     __syncthreads();
     int b[6] = {BOX_EMPTY, BOX_EMPTY, BOX_EMPTY, BOX_EMPTY, BOX_EMPTY, BOX_EMPTY};
-    long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y, k = blockIdx.z;
+    const long N = (long)g.nx * g.ny * g.nz;
+    const int row = (k * g.ny + j) * g.nx;
     if (VEC) {
-        long n = t * 4;
-        if (n < N) {
-            int i = (int)(n % g.nx);
-            long r = n / g.nx;
-            int j = (int)(r % g.ny), k = (int)(r / g.ny);
+        const int i = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
+        if (i < g.nx) {
+            const int n = row + i;
             float x[3][4];
             dvf4(mean, U, K, s_w, N, n, x);
             float o[4];
@@ -138,24 +146,25 @@ k_warp_pca(const T* __restrict__ f0, const T* __restrict__ mean,
                 *reinterpret_cast<float4*>(fpad + pad_index(pd, i, j, k)) = make_float4(o[0], o[1], o[2], o[3]);
             }
         }
-    } else if (t < N) {
-        int i = (int)(t % g.nx);
-        long r = t / g.nx;
-        int j = (int)(r % g.ny), k = (int)(r / g.ny);
-        float x[3];
-        for (int c = 0; c < 3; c++) {
-            float v = mean ? ldg_f(mean + c * N + t) : 0.0f;
-            for (int kk = 0; kk < K; kk++) v = fmaf(s_w[kk], ldg_f(U + ((long)kk * 3 + c) * N + t), v);
-            x[c] = v;
-        }
-        const float o = tri_dense(f0, g, fmaf(x[0], g.inv_sx, (float)i), fmaf(x[1], g.inv_sy, (float)j),
-                                  fmaf(x[2], g.inv_sz, (float)k));
-        if (swp) {
-            if (o != 0.0f) box_add(b, j, i, k);
-            fpad[pad_index(pd, j, i, k)] = o;
-        } else {
-            if (o != 0.0f) box_add(b, i, j, k);
-            fpad[pad_index(pd, i, j, k)] = o;
+    } else {
+        const int i = blockIdx.x * blockDim.x + threadIdx.x;
+        if (i < g.nx) {
+            const int n = row + i;
+            float x[3];
+            for (int c = 0; c < 3; c++) {
+                float v = mean ? ldg_f(mean + c * N + n) : 0.0f;
+                for (int kk = 0; kk < K; kk++) v = fmaf(s_w[kk], ldg_f(U + ((long)kk * 3 + c) * N + n), v);
+                x[c] = v;
+            }
+            const float o = tri_dense(f0, g, fmaf(x[0], g.inv_sx, (float)i), fmaf(x[1], g.inv_sy, (float)j),
+                                      fmaf(x[2], g.inv_sz, (float)k));
+            if (swp) {
+                if (o != 0.0f) box_add(b, j, i, k);
+                fpad[pad_index(pd, j, i, k)] = o;
+            } else {
+                if (o != 0.0f) box_add(b, i, j, k);
+                fpad[pad_index(pd, i, j, k)] = o;
+            }
         }
     }
     box_reduce(b, box_out);
@@ -170,7 +179,7 @@ template <typename T>
 __global__ void __launch_bounds__(kWarpThreads)
 k_warp_batch(const T* __restrict__ f0, const T* __restrict__ mean,
              const T* __restrict__ U, int K, const SolveState* st, Grid g, const View* __restrict__ Vp,
-             long N, float4* __restrict__ fpad4, int* __restrict__ box_out) {
+             float4* __restrict__ fpad4, int* __restrict__ box_out) {
     if (st->phase >= PH_STOP || st->nvalid < 2) return;
     const int swp = Vp ? Vp->xy_swap : 0;
     const Pad pd = solver_pad(g.nx, g.ny, g.nz, swp);
@@ -181,11 +190,10 @@ k_warp_batch(const T* __restrict__ f0, const T* __restrict__ mean,
     }
     __syncthreads();
     int bx[6] = {BOX_EMPTY, BOX_EMPTY, BOX_EMPTY, BOX_EMPTY, BOX_EMPTY, BOX_EMPTY};
-    const long n = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n < N) {
-        const int i = (int)(n % g.nx);
-        const long r = n / g.nx;
-        const int j = (int)(r % g.ny), k = (int)(r / g.ny);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    const long N = (long)g.nx * g.ny * g.nz;
+    if (i < g.nx) {
+        const int n = (k * g.ny + j) * g.nx + i;
         float x[TRIAL_BATCH][3];
 #pragma unroll
         for (int c = 0; c < 3; c++) {
@@ -217,6 +225,19 @@ inline bool aligned(const void* p, unsigned a) { return p == nullptr || ((uintpt
 
 inline unsigned blocks_for(long work) { return (unsigned)((work + kWarpThreads - 1) / kWarpThreads); }
 
+// Launch shape of the solver warps (see k_warp_pca): per = voxels along x per
+// thread; threads per block = the row's threads rounded up to a warp, at most
+// kWarpThreads.
+struct RowLaunch {
+    dim3 grid;
+    unsigned threads;
+};
+inline RowLaunch row_launch(const Grid& g, int per) {
+    const int need = (g.nx + per - 1) / per;
+    const int t = need >= kWarpThreads ? kWarpThreads : ((need + 31) / 32) * 32;
+    return {dim3((unsigned)((need + t - 1) / t), (unsigned)g.ny, (unsigned)g.nz), (unsigned)t};
+}
+
 template <typename T>
 cudaError_t pca_dvf_t(const void* mean, const void* U, int K, const float* w, Grid g, float* dvf,
                       cudaStream_t s) {
@@ -235,14 +256,14 @@ cudaError_t pca_dvf_t(const void* mean, const void* U, int K, const float* w, Gr
 template <typename T>
 cudaError_t warp_pca_t(const void* f0, const void* mean, const void* U, int K, WSrc w, Grid g,
                        const View* Vd, float* fpad, int* box, cudaStream_t s) {
-    long N = (long)g.nx * g.ny * g.nz;
     const unsigned a = sizeof(T) * 4;
     bool vec = (g.nx % 4 == 0) && aligned(mean, a) && aligned(U, a) && aligned(fpad, 16);
     const T* f = static_cast<const T*>(f0);
     const T* m = static_cast<const T*>(mean);
     const T* u = static_cast<const T*>(U);
-    if (vec) k_warp_pca<true, T><<<blocks_for(N / 4), kWarpThreads, 0, s>>>(f, m, u, K, w, g, Vd, N, fpad, box);
-    else k_warp_pca<false, T><<<blocks_for(N), kWarpThreads, 0, s>>>(f, m, u, K, w, g, Vd, N, fpad, box);
+    const RowLaunch L = row_launch(g, vec ? 4 : 1);
+    if (vec) k_warp_pca<true, T><<<L.grid, L.threads, 0, s>>>(f, m, u, K, w, g, Vd, fpad, box);
+    else k_warp_pca<false, T><<<L.grid, L.threads, 0, s>>>(f, m, u, K, w, g, Vd, fpad, box);
     return cudaGetLastError();
 }
 
@@ -275,11 +296,11 @@ cudaError_t launch_warp_pca(const void* f0, const void* mean, const void* U, int
 
 cudaError_t launch_warp_batch(const void* f0, const void* mean, const void* U, int dt, int K,
                               const SolveState* st, Grid g, const View* Vd, float4* fpad4, cudaStream_t s) {
-    long N = (long)g.nx * g.ny * g.nz;
+    const RowLaunch L = row_launch(g, 1);
     int* box = const_cast<int*>(st->box[1]);
-    PCAS_DT_DISPATCH(dt, (k_warp_batch<T><<<blocks_for(N), kWarpThreads, 0, s>>>(
+    PCAS_DT_DISPATCH(dt, (k_warp_batch<T><<<L.grid, L.threads, 0, s>>>(
                               static_cast<const T*>(f0), static_cast<const T*>(mean),
-                              static_cast<const T*>(U), K, st, g, Vd, N, fpad4, box),
+                              static_cast<const T*>(U), K, st, g, Vd, fpad4, box),
                           cudaGetLastError()))
 }
 

@@ -65,6 +65,20 @@ def test_workspace_bytes_host_only(lib):
     need = npad * (4 + 16) + M * (5 * 4 + 32) + cap * (4 + 4 * 3)   # f, 4 candidates, 5 projections,
     assert need <= n < need + 2_000_000 and n % 256 == 0            # ray table, compacted voxels
     assert P.workspace_bytes(vol, cb, 0) == 0 and P.workspace_bytes(vol, cb, 9) == 0
+    # room for the y-fastest layout too: a non-square grid takes the larger of the two
+    v2 = S.volume(200, 300, 50, 2.0, 2.0, 2.0)
+    pa = ((200 + 9) // 4 * 4) * 304 * 54
+    pb = ((300 + 9) // 4 * 4) * 204 * 54
+    assert P.workspace_bytes(v2, cb, 3) >= max(pa, pb) * (4 + 16)
+
+
+def test_volume_size_limits(lib):
+    """32-bit voxel offsets: ny, nz <= 65535 and the halo layout below 2^31 elements."""
+    cb = S.cone_beam(64, 48, 1.0, 1.0)
+    assert P.workspace_bytes(S.volume(8, 65536, 4, 1, 1, 1), cb, 1) == 0
+    assert P.workspace_bytes(S.volume(8, 4, 65536, 1, 1, 1), cb, 1) == 0
+    assert P.workspace_bytes(S.volume(1300, 1300, 1260, 1, 1, 1), cb, 1) == 0   # (1310)(1304)(1264) > 2^31
+    assert P.workspace_bytes(S.volume(1024, 1024, 1024, 1, 1, 1), cb, 1) > 0
 
 
 FAKE = C.c_void_p(0x1000)    # never dereferenced: every call below fails its host checks
