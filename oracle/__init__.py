@@ -9,7 +9,7 @@ module only compiles it with gcc and marshals numpy arrays through ctypes.
 
 Parity status of each routine (what pins it is in ``tests/test_oracle_*.py``):
   pca_dvf, warp_volume, trilinear, trilinear_grad, drr_forward, drr_ray,
-  drr_adjoint, intensity_fit, cost, cost_grad, grad_forward_mode,
+  siddon_forward, siddon_ray, drr_adjoint, intensity_fit, cost, cost_grad, grad_forward_mode,
   warp_adjoint, cost_grad_f0, solve_projection, localize_tumor, lp_fit,
   lp_predict -- all pinned.
 """
@@ -83,6 +83,8 @@ def lib():
                 ("oracle_drr_forward", C.c_int, [_D, C.POINTER(Vol), C.POINTER(CB), C.c_double, _D]),
                 ("oracle_drr_ray", C.c_double, [_D, C.POINTER(Vol), C.POINTER(CB), C.c_double, C.c_int, C.c_int]),
                 ("oracle_drr_adjoint", C.c_int, [_D, C.POINTER(Vol), C.POINTER(CB), C.c_double, _D]),
+                ("oracle_siddon_forward", C.c_int, [_D, C.POINTER(Vol), C.POINTER(CB), _D]),
+                ("oracle_siddon_ray", C.c_double, [_D, C.POINTER(Vol), C.POINTER(CB), C.c_int, C.c_int]),
                 ("oracle_intensity_fit", C.c_int, [_D, _D, C.c_long, _D, _D]),
                 ("oracle_cost", C.c_double, [_D, _D, C.c_long, C.c_double, C.c_double]),
                 ("oracle_cost_grad", C.c_int, [_D, _D, _D, C.c_int, _D, _D, C.POINTER(Vol), C.POINTER(CB),
@@ -176,6 +178,20 @@ def drr_ray(f, vol, cb, step, iu, iv):
     f = _d(f).ravel()
     return lib().oracle_drr_ray(_p(f), C.byref(vol_struct(vol)), C.byref(cb_struct(cb)),
                                 float(step), int(iu), int(iv))
+
+
+def siddon_forward(f, vol, cb):
+    """Exact line integrals of the piecewise-constant volume (Sec. II.B)."""
+    f = _d(f).ravel()
+    p = np.empty(cb["nu"] * cb["nv"])
+    _check(lib().oracle_siddon_forward(_p(f), C.byref(vol_struct(vol)), C.byref(cb_struct(cb)), _p(p)),
+           "siddon_forward")
+    return p
+
+
+def siddon_ray(f, vol, cb, iu, iv):
+    f = _d(f).ravel()
+    return lib().oracle_siddon_ray(_p(f), C.byref(vol_struct(vol)), C.byref(cb_struct(cb)), int(iu), int(iv))
 
 
 def drr_adjoint(img, vol, cb, step):

@@ -210,6 +210,73 @@ int oracle_drr_forward(const double* f, const ovol* vol, const ocb* cb, double s
     return 0;
 }
 
+/* ----------------------------------------- Siddon projector (Sec. II.B) */
+static int cmp_double(const void* a, const void* b) {
+    double x = *(const double*)a, y = *(const double*)b;
+    return (x > y) - (x < y);
+}
+
+double oracle_siddon_ray(const double* f, const ovol* vol, const ocb* cb, int iu, int iv) {
+    oframe F;
+    double dh[3];
+    view_frame(cb, &F);
+    ray_dir(cb, &F, iu, iv, dh);
+    double o[3] = {vol->ox, vol->oy, vol->oz}, s[3] = {vol->sx, vol->sy, vol->sz};
+    int n[3] = {vol->nx, vol->ny, vol->nz};
+    /* the ray's parameter interval inside the union of the voxel cubes */
+    double tin = 0.0, tout = INFINITY;
+    for (int c = 0; c < 3; c++) {
+        double lo = o[c] - 0.5 * s[c], hi = o[c] + (n[c] - 0.5) * s[c];
+        if (dh[c] == 0.0) {
+            if (F.S[c] < lo || F.S[c] > hi) return 0.0;
+            continue;
+        }
+        double t1 = (lo - F.S[c]) / dh[c], t2 = (hi - F.S[c]) / dh[c];
+        if (t1 > t2) { double t = t1; t1 = t2; t2 = t; }
+        if (t1 > tin) tin = t1;
+        if (t2 < tout) tout = t2;
+    }
+    if (!(tin < tout)) return 0.0;
+    /* every crossing with a voxel face plane inside (tin, tout), plus the ends */
+    long cap = 2 + (long)(n[0] + 1) + (n[1] + 1) + (n[2] + 1);
+    double* t = (double*)malloc(sizeof(double) * cap);
+    long m = 0;
+    t[m++] = tin;
+    t[m++] = tout;
+    for (int c = 0; c < 3; c++) {
+        if (dh[c] == 0.0) continue;
+        for (int l = 0; l <= n[c]; l++) {
+            double tc = (o[c] + (l - 0.5) * s[c] - F.S[c]) / dh[c];
+            if (tc > tin && tc < tout) t[m++] = tc;
+        }
+    }
+    qsort(t, m, sizeof(double), cmp_double);
+    double sum = 0.0;
+    for (long e = 0; e + 1 < m; e++) {
+        double len = t[e + 1] - t[e];
+        if (!(len > 0.0)) continue;
+        double tm = 0.5 * (t[e] + t[e + 1]);
+        long idx[3];
+        int inside = 1;
+        for (int c = 0; c < 3; c++) {
+            idx[c] = (long)floor((F.S[c] + tm * dh[c] - o[c]) / s[c] + 0.5);
+            if (idx[c] < 0 || idx[c] >= n[c]) inside = 0;
+        }
+        if (inside) sum += len * f[(idx[2] * n[1] + idx[1]) * n[0] + idx[0]];
+    }
+    free(t);
+    return sum;
+}
+
+int oracle_siddon_forward(const double* f, const ovol* vol, const ocb* cb, double* p) {
+    if (!vol_ok(vol) || !cb_ok(vol, cb, 1.0) || !f || !p) return 1;
+#pragma omp parallel for collapse(2) schedule(dynamic, 4)
+    for (int iv = 0; iv < cb->nv; iv++)
+        for (int iu = 0; iu < cb->nu; iu++)
+            p[(long)iv * cb->nu + iu] = oracle_siddon_ray(f, vol, cb, iu, iv);
+    return 0;
+}
+
 /* P^T: for every (ray, sample) pair of P, add step * img(ray) * weight to the
  * eight taps of the sample -- the transpose of the sum in oracle_drr_ray. */
 int oracle_drr_adjoint(const double* img, const ovol* vol, const ocb* cb, double step, double* g) {

@@ -67,6 +67,14 @@ void oracle_trilinear_grad(const double* f, const ovol* vol, double q1, double q
 int oracle_drr_forward(const double* f, const ovol* vol, const ocb* cb, double step, double* p);
 /* One ray of P (sampled parity checks at full size). */
 double oracle_drr_ray(const double* f, const ovol* vol, const ocb* cb, double step, int iu, int iv);
+/* Siddon's exact radiological path (Sec. II.B renders its simulated projections
+ * with it): the integral of the piecewise-constant volume (voxel (i,j,k) = its
+ * value on the cube of side s centred on it, zero outside) along the ray from
+ * S through the centre of pixel (iu, iv).  Plane crossings of the ray with all
+ * voxel faces, sorted; each segment between consecutive crossings adds its
+ * length times the value of the voxel containing its midpoint. */
+int oracle_siddon_forward(const double* f, const ovol* vol, const ocb* cb, double* p);
+double oracle_siddon_ray(const double* f, const ovol* vol, const ocb* cb, int iu, int iv);
 /* P^T: the literal transpose of oracle_drr_forward (scatter form). g overwritten. */
 int oracle_drr_adjoint(const double* img, const ovol* vol, const ocb* cb, double step, double* g);
 /* Eq. (A.1): least squares of p on [y, 1]. Returns 2 if Y^T Y is singular. */
