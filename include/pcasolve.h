@@ -103,6 +103,17 @@ int warp_volume(const float* f0, const float* dvf, const pcas_vol* vol, float* f
 int drr_forward(const float* f, const pcas_vol* vol, const pcas_cb* cb, double step_mm,
                 float* p, void* stream);
 
+/* Siddon's exact radiological path, the projector Sec. II.B simulates its
+ * measured projections with: p(ray) = the integral along the ray from the
+ * source through the pixel centre of the piecewise-constant volume (voxel
+ * (i,j,k) = f on the cube of side (sx, sy, sz) centred on it, zero outside).
+ * Used to render measured images without the inverse crime of projecting
+ * with the solver's own P; not on the solver path.  Voxel traversal and the
+ * sum in double precision, p rounded to float.  f, p: device.  Asynchronous.
+ * Errors: PCAS_ERR_INVALID_ARG for a NULL pointer, an invalid volume or
+ * view, or a volume not entirely in front of the source. */
+int drr_siddon(const float* f, const pcas_vol* vol, const pcas_cb* cb, float* p, void* stream);
+
 /* P^T, the exact transpose of drr_forward (gradient formula below Eq. A.2),
  * computed in gather form without atomics: g[v] = step sum over rays and
  * samples of img(ray) times the trilinear weight of voxel v.
@@ -276,7 +287,8 @@ enum {
     PCAS_K_DRR_BATCH = 11,   /* four candidates projected and tested at once    */
     PCAS_K_GRAD_F0 = 12,     /* dJ/df0: full backprojection + warp transpose    */
     PCAS_K_GRAPH = 13,       /* kernels run inside device-driven (graph) solves  */
-    PCAS_K_COUNT = 14
+    PCAS_K_SIDDON = 14,      /* drr_siddon                                      */
+    PCAS_K_COUNT = 15
 };
 int pcas_profile(int on);
 int pcas_profile_read(int kind, long long* launches, double* total_ms);

@@ -460,6 +460,32 @@ int drr_forward(const float* f, const pcas_vol* vol, const pcas_cb* cb, double s
     return PCAS_OK;
 }
 
+int drr_siddon(const float* f, const pcas_vol* vol, const pcas_cb* cb, float* p, void* stream) {
+    PCAS_TRY(check_vol(vol));
+    PCAS_TRY(check_ptr(f, "f"));
+    PCAS_TRY(check_ptr(p, "p"));
+    View V;
+    PCAS_TRY(make_view(vol, cb, 1.0, &V));        // geometry checks (volume ahead of the source)
+    SidView D;
+    const double sa = sin(cb->angle_rad), ca = cos(cb->angle_rad);
+    const double S[3] = {cb->sad * sa, -cb->sad * ca, 0.0};
+    const double ew[3] = {-sa, ca, 0.0}, eu[3] = {ca, sa, 0.0}, ev[3] = {0.0, 0.0, 1.0};
+    for (int c = 0; c < 3; c++) { D.S[c] = S[c]; D.ew[c] = ew[c]; D.eu[c] = eu[c]; D.ev[c] = ev[c]; }
+    D.sdd = cb->sdd;
+    D.u0 = cb->off_u - 0.5 * (cb->nu - 1) * cb->du;
+    D.v0 = cb->off_v - 0.5 * (cb->nv - 1) * cb->dv;
+    D.du = cb->du;
+    D.dv = cb->dv;
+    D.o[0] = vol->ox; D.o[1] = vol->oy; D.o[2] = vol->oz;
+    D.s[0] = vol->sx; D.s[1] = vol->sy; D.s[2] = vol->sz;
+    D.n[0] = vol->nx; D.n[1] = vol->ny; D.n[2] = vol->nz;
+    D.nu = cb->nu;
+    D.nv = cb->nv;
+    cudaStream_t s = as_stream(stream);
+    PCAS_LAUNCH(PCAS_K_SIDDON, s, launch_drr_siddon(f, D, p, s));
+    return PCAS_OK;
+}
+
 int drr_adjoint(const float* img, const pcas_vol* vol, const pcas_cb* cb, double step_mm, float* g,
                 void* stream) {
     PCAS_TRY(check_vol(vol));

@@ -388,6 +388,15 @@ cudaError_t launch_warp_pca(const void* f0, const void* mean, const void* U, int
 cudaError_t launch_warp_batch(const void* f0, const void* mean, const void* U, int dt, int K,
                               const SolveState* st, Grid g, const View* Vd, float4* fpad4, cudaStream_t s);
 cudaError_t launch_drr_plain(const float* f, Grid g, const View& V, float* p, cudaStream_t s);
+// Siddon geometry in double precision (world mm): source, unit axes, pixel
+// grid and the voxel grid (origin = centre of voxel (0,0,0)).
+struct SidView {
+    double S[3], ew[3], eu[3], ev[3];
+    double sdd, u0, du, v0, dv;
+    double o[3], s[3];
+    int n[3], nu, nv;
+};
+cudaError_t launch_drr_siddon(const float* f, const SidView& V, float* p, cudaStream_t s);
 // Solver projector.  mode 0: first evaluation into buffer cur; mode 1: one
 // trial volume; mode 4: the four-volume batch (st->nvalid of them on the
 // schedule).  Vh: the view on the host (grid size), Vd: the same in device

@@ -5,7 +5,7 @@ library.  Device arrays are torch CUDA tensors (float32, contiguous); the
 current torch stream is passed to the library.  There is no CPU fallback: if
 the library is missing, loading raises.
 
-Names follow the C ABI: pca_dvf, warp_volume, drr_forward, drr_adjoint,
+Names follow the C ABI: pca_dvf, warp_volume, drr_forward, drr_siddon, drr_adjoint,
 cost_grad, solve_projection, localize_tumor, lp_fit, lp_predict.
 """
 from __future__ import annotations
@@ -66,6 +66,7 @@ _SIGS = {
     "pca_dvf": (C.c_int, [_P, _P, C.c_int, _D, C.POINTER(Vol), _P, _P]),
     "warp_volume": (C.c_int, [_P, _P, C.POINTER(Vol), _P, _P]),
     "drr_forward": (C.c_int, [_P, C.POINTER(Vol), C.POINTER(CB), C.c_double, _P, _P]),
+    "drr_siddon": (C.c_int, [_P, C.POINTER(Vol), C.POINTER(CB), _P, _P]),
     "drr_adjoint": (C.c_int, [_P, C.POINTER(Vol), C.POINTER(CB), C.c_double, _P, _P]),
     "cost_grad": (C.c_int, [_P, _P, _P, C.c_int, _D, _P, C.POINTER(Vol), C.POINTER(CB), C.c_double,
                             _D, _D, _D, _P, C.c_size_t, _P]),
@@ -102,7 +103,8 @@ _SIGS = {
 
 # kernel classes of pcas_profile_read (include/pcasolve.h)
 KERNELS = ["warp_pca", "drr_solver", "resid", "adjoint_grad", "drr_forward", "drr_adjoint",
-           "pca_dvf", "warp_volume", "localize", "init", "warp_batch", "drr_batch", "grad_f0", "graph"]
+           "pca_dvf", "warp_volume", "localize", "init", "warp_batch", "drr_batch", "grad_f0", "graph",
+           "siddon"]
 
 
 def lib():
@@ -244,6 +246,18 @@ def drr_forward(f, vol, cb, step, out=None, stream=None):
         out = torch.empty(g.nu * g.nv, dtype=torch.float32, device=f.device)
     _check(lib().drr_forward(_dev(f, "f", _nvox(vol)), C.byref(vol_struct(vol)), C.byref(g),
                              float(step), _dev(out, "p", g.nu * g.nv), _stream(stream)))
+    return out
+
+
+def drr_siddon(f, vol, cb, out=None, stream=None):
+    """Siddon's exact radiological path (Sec. II.B's simulation projector), for
+    rendering measured images without the inverse crime."""
+    import torch
+    g = cb_struct(cb)
+    if out is None:
+        out = torch.empty(g.nu * g.nv, dtype=torch.float32, device=f.device)
+    _check(lib().drr_siddon(_dev(f, "f", _nvox(vol)), C.byref(vol_struct(vol)), C.byref(g),
+                            _dev(out, "p", g.nu * g.nv), _stream(stream)))
     return out
 
 
