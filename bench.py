@@ -58,9 +58,14 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--irregular", action="store_true", help="irregular breathing trace")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="sequence", choices=["sequence", "precision", "batch"],
-                    help="sequence: the default line; precision: float32 vs bfloat16 vs float16 storage; "
+    ap.add_argument("--workload", default="sequence", choices=["sequence", "fluoro", "precision", "batch"],
+                    help="sequence: the default line; fluoro: the same sequence at one fixed gantry angle "
+                         "(fluoroscopy); precision: float32 vs bfloat16 vs float16 storage; "
                          "batch: 64 uneven solves in one graph launch vs one after another")
+    ap.add_argument("--projector", default="siddon", choices=["siddon", "trilinear"],
+                    help="renderer of the measured images: Siddon's exact path (Sec. II.B, no inverse "
+                         "crime) or the solver's own trilinear projector")
+    ap.add_argument("--angle-deg", type=float, default=90.0, help="gantry angle of the fluoro workload")
     return ap.parse_args()
 
 
@@ -72,6 +77,18 @@ def dist_env():
 
 
 # ----------------------------------------------------------------- inputs
+def workload_name(args):
+    base = WORKLOAD["name"] + ("-irregular" if args.irregular else "-regular")
+    if args.workload == "fluoro":
+        base = base.replace("sequence", "fluoro") + f"-{args.angle_deg:g}deg"
+    return base + ("-siddon" if args.projector == "siddon" else "-trilinear")
+
+
+def fixed_angles(args, angles):
+    """The fluoro workload projects every frame at one gantry angle."""
+    return np.full_like(angles, np.deg2rad(args.angle_deg)) if args.workload == "fluoro" else angles
+
+
 def make_inputs(irregular: bool):
     from paper_1102_1712_gb300 import synth as S
     W = WORKLOAD
@@ -221,6 +238,7 @@ def run_ours(args, ws_, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     vol, f0, c_ref, U, trace, train, angles = make_inputs(args.irregular)
+    angles = fixed_angles(args, angles)
     K, N = WORKLOAD["K"], f0.size
     d = WORKLOAD["det"]
     M = d[0] * d[1]
@@ -231,12 +249,16 @@ def run_ours(args, ws_, rank, local):
     n_used = W_ + K_
     if n_used > WORKLOAD["n_proj"]:
         raise SystemExit(f"warmup + steps must be <= {WORKLOAD['n_proj']}")
-    # measured projections: P f(w_true(t)) rendered by the library + seeded noise
+    # measured projections: the planted volume f(w_true(t)) rendered by Siddon's
+    # projector (or the solver's own) in the library + seeded noise
     ys = torch.empty((n_used, M), dtype=torch.float32, device=dev)
     c_true = np.zeros((n_used, 3))
     for t in range(n_used):
         f = P.warp_volume(tf0, P.pca_dvf(None, tU, trace[t], vol), vol)
-        p = P.drr_forward(f, vol, view(angles[t]), step)
+        if args.projector == "siddon":
+            p = P.drr_siddon(f, vol, view(angles[t]))
+        else:
+            p = P.drr_forward(f, vol, view(angles[t]), step)
         sigma = WORKLOAD["noise"] * float(p.abs().max())
         ys[t] = p + torch.from_numpy(S.gaussian_noise(M, sigma, seed=1000 * WORKLOAD["seeds"]["noise"] + t)).to(dev)
         c_true[t], _ = P.localize_tumor(None, tU, trace[t], vol, c_ref)
@@ -363,10 +385,13 @@ def run_ours(args, ws_, rank, local):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seeded ellipsoid phantom, smoothed random eigen-DVFs, sinusoidal trace; "
-                "projections rendered by this library + 1% noise)",
-        "config": {"workload": WORKLOAD["name"] + ("-irregular" if args.irregular else "-regular"),
+                f"projections rendered by this library's {args.projector} projector + 1% noise)",
+        "config": {"workload": workload_name(args),
                    "volume": "256x256x100 @ 2x2x2.5 mm", "K": K, "detector": "512x384 @ 0.776 mm",
-                   "step_mm": step, "projections": f"{W_}+{K_} of 600 over 360 deg",
+                   "step_mm": step,
+                   "projections": (f"{W_}+{K_} of 600 at {args.angle_deg:g} deg" if args.workload == "fluoro"
+                                   else f"{W_}+{K_} of 600 over 360 deg"),
+                   "measured_images": args.projector,
                    "solver": "mu0=0.2 alpha=0.1 beta=0.5 mu_min=0.01 max_iter=10",
                    "l2": "inputs larger than L2 (motion model 236 MB streamed per evaluation)",
                    "parallelism": "replicas" if ws_ > 1 else "single"},
@@ -427,14 +452,18 @@ def run_reference(args, ws_, rank):
     from paper_1102_1712_gb300 import synth as S
     O.build()
     vol, f0, c_ref, U, trace, train, angles = make_inputs(args.irregular)
+    angles = fixed_angles(args, angles)
     step = step_mm()
     c_lp = O.lp_fit(train, 2)
-    d = WORKLOAD["det"]
     done, t_total, budget = 0, 0.0, 150.0
     for i in range(args.warmup + args.steps):
         t = 2 + i
         cb = view(angles[t])
-        p = O.drr_forward(O.warp_volume(f0, O.pca_dvf(None, U, trace[t], vol), vol), vol, cb, step)
+        f_true = O.warp_volume(f0, O.pca_dvf(None, U, trace[t], vol), vol)
+        if args.projector == "siddon":
+            p = O.siddon_forward(f_true, vol, cb)
+        else:
+            p = O.drr_forward(f_true, vol, cb, step)
         y = (p + S.gaussian_noise(p.size, WORKLOAD["noise"] * np.abs(p).max(),
                                   seed=1000 * WORKLOAD["seeds"]["noise"] + t, dtype=np.float64)).astype(np.float32)
         w0 = O.lp_predict(np.stack([trace[t - 1], trace[t - 2]]), c_lp)
@@ -453,7 +482,7 @@ def run_reference(args, ws_, rank):
     return {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "projections/s",
             "n_gpus": 1, "steps": done, "warmup": args.warmup, "ms_per_step": round(1e3 * t_total / done, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic, same workload as our arm", "config": {"workload": WORKLOAD["name"]},
+            "data": "synthetic, same workload as our arm", "config": {"workload": workload_name(args)},
             "cpu_baseline": {"value": round(value, 5), "unit": "projections/s", "cores": os.cpu_count(),
                              "kind": "oracle",
                              "sample": f"{done} projections of the workload, full solves, 150 s budget"},
@@ -492,7 +521,8 @@ def run_precision(args, local):
     ys = torch.empty((n_used, M), dtype=torch.float32, device=dev)
     c_true = np.zeros((n_used, 3))
     for t in range(n_used):
-        p = P.drr_forward(P.warp_volume(tf0, P.pca_dvf(None, tU, trace[t], vol), vol), vol, views[t], step)
+        f = P.warp_volume(tf0, P.pca_dvf(None, tU, trace[t], vol), vol)
+        p = P.drr_siddon(f, vol, views[t]) if args.projector == "siddon" else P.drr_forward(f, vol, views[t], step)
         sigma = W["noise"] * float(p.abs().max())
         ys[t] = p + torch.from_numpy(S.gaussian_noise(M, sigma, seed=1000 * W["seeds"]["noise"] + t)).to(dev)
         c_true[t], _ = P.localize_tumor(None, tU, trace[t], vol, c_ref)
@@ -559,7 +589,7 @@ def run_precision(args, local):
             "warmup": W_, "ms_per_step": bf["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16 storage, f32 arithmetic",
             "data": "synthetic (seeded phantom, coarse-grid smoothed eigen-DVFs, irregular trace; "
-                    "projections rendered by this library in float32 + 1% noise)",
+                    f"projections rendered by this library's {args.projector} projector + 1% noise)",
             "config": {"workload": W["name"], "volume": "512x512x160 @ 1x1x2 mm", "K": K,
                        "detector": "1024x768 @ 0.388 mm", "step_mm": step,
                        "projections": f"{W_}+{K_} of 300 over 360 deg, irregular"},
@@ -602,8 +632,9 @@ def run_batch(args, local):
                           c_ref=c_ref, w_true=w_true, step=0.5 * min(vol["sx"], vol["sy"], vol["sz"])))
     for i, pb in enumerate(probs):
         M = pb["cb"]["nu"] * pb["cb"]["nv"]
-        p = P.drr_forward(P.warp_volume(pb["f0"], P.pca_dvf(None, pb["U"], pb["w_true"], pb["vol"]), pb["vol"]),
-                          pb["vol"], pb["cb"], pb["step"])
+        f = P.warp_volume(pb["f0"], P.pca_dvf(None, pb["U"], pb["w_true"], pb["vol"]), pb["vol"])
+        p = (P.drr_siddon(f, pb["vol"], pb["cb"]) if args.projector == "siddon"
+             else P.drr_forward(f, pb["vol"], pb["cb"], pb["step"]))
         sigma = W["noise"] * float(p.abs().max())
         pb["y"] = p + torch.from_numpy(S.gaussian_noise(M, sigma, seed=300 + i)).to(dev)
         pb["c_true"], _ = P.localize_tumor(None, pb["U"], pb["w_true"], pb["vol"], pb["c_ref"])
@@ -655,7 +686,7 @@ def run_batch(args, local):
             "warmup": max(args.warmup, 1), "ms_per_step": round(ms_b / reps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (64 seeded phantoms, 6 seeded eigenvector models, random angles, w ~ N(0,1); "
-                    "projections rendered by this library + 1% noise)",
+                    f"projections rendered by this library's {args.projector} projector + 1% noise)",
             "config": {"workload": W["name"], "solves_per_step": n,
                        "volumes": "128^2x64 / 192^2x96 / 256^2x128", "K": "3 / 5",
                        "detectors": "256x192 / 512x384 / 768x576 / 1024x768", "start": "w = 0",
