@@ -154,8 +154,8 @@ int cost_grad_f0(const float* f0, const float* mean, const float* U, int K, cons
  * the library, which every GPU that loads the library holds until exit; no
  * call here allocates.  Volumes and detectors whose scratch
  * (pcas_workspace_bytes) exceeds that size are rejected with
- * PCAS_ERR_INVALID_ARG (e.g. 96x96x48 voxels with a 256x192 detector fit;
- * 256x256x100 does not).  The first call on each device looks
+ * PCAS_ERR_INVALID_ARG (e.g. 80x80x40 voxels with a 192x144 detector and
+ * K = 3 fit; 256x256x100 does not).  The first call on each device looks
  * up the array's device address (cudaGetSymbolAddress, which also loads the
  * library's device code there): make that first call before any stream
  * capture.  All calls on a device share the array and it keeps the last
@@ -272,6 +272,53 @@ int lp_predict(const double* hist, const double* c, int K, int L, double* w0);
  * pcas_profile_read() returns the launches and the summed event time in ms
  * of one class since the last reset; it waits for the recorded events.
  * These calls are host-side and thread-safe. */
+/* ---------------------------------------------------------------- autotuner
+ * Launch shapes of the solver kernels, kept per size bucket (volume extents
+ * in steps of 32, 32, 16 voxels, detector extents in steps of 64 pixels, K,
+ * storage type).  No counterpart in the paper; they change speed only.
+ *   ray_lw1, ray_lw4  log2 of a warp's patch width on the detector (2..4):
+ *                     (1 << lw) x (32 >> lw) pixels, for the one-volume and
+ *                     the four-candidate projector
+ *   chunk             sample indices per shared-memory chunk of the
+ *                     four-candidate projector (even, 2..64)
+ *   voxel_tile        voxel tile of the gradient pass: 0 = 8x8x4, 1 = 16x4x4,
+ *                     2 = 32x4x2, 3 = 16x8x2, 4 = 32x8x1, 5 = 64x4x1
+ *   gather_per_sm     blocks of the gradient gather per SM (1..26)
+ *   swap1, swap4      layout of the one-volume / four-candidate solver
+ *                     volumes per 22.5-degree bin of the gantry angle modulo
+ *                     180 degrees (bin b centred on 22.5 b): 0 = x fastest,
+ *                     1 = y fastest
+ * Every call takes the entry of its bucket, or the defaults (3, 3, 16, 0, 8,
+ * y fastest in bins 3..5) when there is none; a device-driven solver takes
+ * the entry in force when it is created.  Other shapes reorder floating-point
+ * sums: results can differ by rounding between shapes, and are reproducible
+ * for a fixed table. */
+typedef struct {
+    int ray_lw1, ray_lw4, chunk, voxel_tile, gather_per_sm;
+    unsigned char swap1[8], swap4[8];
+} pcas_tuning;
+
+/* Measures shapes on this problem and stores the fastest in its bucket:
+ * trial solves (solve_projection with max_iter capped at 3, from w_init, at
+ * the centre angle of a bin), every kernel timed with CUDA events; first the
+ * two layouts of each bin, then the patch widths, the chunk, the voxel tile
+ * and the gather size, each chosen by the time of the kernels it drives
+ * (about 60 trial solves).  f0, mean, U, y, ws: device, as solve_projection
+ * (ws of pcas_workspace_bytes); w_init: host, K doubles or NULL (zeros);
+ * out (host, may be NULL) receives the stored entry.  Synchronous.  Bins
+ * whose view is invalid (volume not in front of the source) keep their
+ * layouts.  Call it from one thread, outside stream capture. */
+int pcas_autotune(const void* f0, const void* mean, const void* U, int dtype, int K,
+                  const pcas_vol* vol, const pcas_cb* cb, const pcas_params* params,
+                  const double* w_init, const float* y, void* ws, size_t ws_bytes,
+                  pcas_tuning* out, void* stream);
+/* The entry in force for a problem's bucket (the defaults if none). */
+int pcas_tuning_get(const pcas_vol* vol, const pcas_cb* cb, int K, int dtype, pcas_tuning* out);
+/* Stores an entry (validated: PCAS_ERR_INVALID_ARG when a field is out of range). */
+int pcas_tuning_set(const pcas_vol* vol, const pcas_cb* cb, int K, int dtype, const pcas_tuning* t);
+/* Forgets every stored entry. */
+int pcas_tuning_clear(void);
+
 enum {
     PCAS_K_WARP_PCA = 0,     /* fused Eq. (1) + (A.5) into the solver volume   */
     PCAS_K_DRR_SOLVER = 1,   /* solver P with fused moments / Armijo test      */

@@ -7,6 +7,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -48,7 +49,32 @@ cudaEvent_t* g_ev = nullptr;           // 2 * kProfSlots events, created once
 int g_ev_kind[kProfSlots];
 int g_ev_used = 0;
 
+// Per-thread event timing used by the autotuner (independent of the global
+// profiler; the autotuner's launches are not counted there).
+constexpr int kLocalSlots = 8192;
+constexpr int kLocalBase = 1 << 24;
+struct LocalTimer {
+    cudaEvent_t ev[2 * kLocalSlots];
+    int kind[kLocalSlots];
+    int used = 0;
+    int created = 0;           // events created so far (lazily)
+};
+thread_local LocalTimer* t_local = nullptr;
+
 int prof_begin(int kind, cudaStream_t s) {
+    if (t_local) {
+        LocalTimer& L = *t_local;
+        if (L.used >= kLocalSlots) return -1;
+        const int slot = L.used++;
+        if (2 * slot + 1 >= L.created) {
+            if (cudaEventCreate(&L.ev[2 * slot]) != cudaSuccess) return -1;
+            if (cudaEventCreate(&L.ev[2 * slot + 1]) != cudaSuccess) return -1;
+            L.created = 2 * slot + 2;
+        }
+        L.kind[slot] = kind;
+        cudaEventRecord(L.ev[2 * slot], s);
+        return kLocalBase + slot;
+    }
     std::lock_guard<std::mutex> lk(g_prof_mutex);
     g_launches[kind]++;
     if (!g_prof_on || !g_ev || g_ev_used >= kProfSlots) return -1;
@@ -60,6 +86,10 @@ int prof_begin(int kind, cudaStream_t s) {
 
 void prof_end(int slot, cudaStream_t s) {
     if (slot < 0) return;
+    if (slot >= kLocalBase) {
+        cudaEventRecord(t_local->ev[2 * (slot - kLocalBase) + 1], s);
+        return;
+    }
     cudaEventRecord(g_ev[2 * slot + 1], s);
 }
 
@@ -145,7 +175,7 @@ int make_view(const pcas_vol* vol, const pcas_cb* cb, double step, View* V) {
     V->nu = cb->nu;
     V->nv = cb->nv;
     V->step = (float)step;
-    V->xy_swap = fabs(sa) > fabs(ca) ? 1 : 0;
+    V->swap1 = V->swap4 = 0;                // set per launch shape by set_layouts
     return PCAS_OK;
 }
 
@@ -179,7 +209,7 @@ Layout layout(const pcas_vol* vol, const pcas_cb* cb, int K) {
     L.part_drr = off; off += align256((size_t)drr_blocks(cb->nu, cb->nv) * DRR_PART_VALS * sizeof(double));
     L.part_res = off; off += align256((size_t)resid_blocks(cb->nu, cb->nv) * sizeof(double));
     L.part_adj = off; off += align256((size_t)ADJ_MAX_BLOCKS * PCAS_KMAX * sizeof(double));
-    const size_t nt = (size_t)adj_tiles(vol->nx, vol->ny, vol->nz), cap = nt * 256;
+    const size_t nt = (size_t)adj_tiles_max(vol->nx, vol->ny, vol->nz), cap = nt * 256;
     L.act_idx = off; off += align256(cap * sizeof(int));                  // compacted voxels
     L.act_h = off; off += align256((size_t)K * cap * sizeof(float));
     L.tile_count = off; off += align256(nt * sizeof(int));
@@ -223,13 +253,67 @@ int bind_ws(void* ws, size_t ws_bytes, const pcas_vol* vol, const pcas_cb* cb, i
     return PCAS_OK;
 }
 
-int adjoint_block_cap() {
-    int dev = 0, sms = 0, per_sm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 1024;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1024;
-    if (cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess) return 1024;
-    int cap = sms * (per_sm / 256);
-    return cap > 0 ? cap : 1024;
+// ------------------------------------------------------------ launch shapes
+// Default shapes: 8 x 4 warp patches, 16-sample chunks, 8 x 8 x 4 voxel tiles,
+// eight gather blocks per SM, y-fastest solver volumes for angles near 90
+// (bins 67.5 ... 112.5 degrees).
+Tune default_tune() {
+    Tune T;
+    T.lw1 = 3;
+    T.lw4 = 3;
+    T.chunk = 16;
+    T.vt = 0;
+    T.adj_mult = 8;
+    for (int b = 0; b < NBIN; b++) T.swap1[b] = T.swap4[b] = (b >= 3 && b <= 5) ? 1 : 0;
+    return T;
+}
+
+// 22.5-degree bin of the gantry angle modulo 180 degrees, bins centred on
+// 0, 22.5, ..., 157.5 degrees.
+int angle_bin(double angle) {
+    double a = fmod(angle, M_PI);
+    if (a < 0) a += M_PI;
+    int b = (int)floor(a / (M_PI / NBIN) + 0.5);
+    return b % NBIN;
+}
+
+void set_layouts(View& V, const Tune& T, double angle) {
+    const int b = angle_bin(angle);
+    V.swap1 = T.swap1[b];
+    V.swap4 = T.swap4[b];
+}
+
+// Size buckets: volume extents in steps of 32 (x, y) and 16 (z) voxels,
+// detector extents in steps of 64 pixels, K and the storage type.
+struct BucketKey {
+    int bx, by, bz, bu, bv, K, dt;
+    bool operator<(const BucketKey& o) const {
+        const int a[7] = {bx, by, bz, bu, bv, K, dt}, c[7] = {o.bx, o.by, o.bz, o.bu, o.bv, o.K, o.dt};
+        for (int i = 0; i < 7; i++)
+            if (a[i] != c[i]) return a[i] < c[i];
+        return false;
+    }
+};
+BucketKey bucket_of(const pcas_vol* vol, const pcas_cb* cb, int K, int dt) {
+    return {(vol->nx + 31) / 32, (vol->ny + 31) / 32, (vol->nz + 15) / 16, (cb->nu + 63) / 64, (cb->nv + 63) / 64,
+            K, dt};
+}
+std::mutex g_tune_mutex;
+std::map<BucketKey, Tune> g_tunes;
+
+Tune tune_for(const pcas_vol* vol, const pcas_cb* cb, int K, int dt) {
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    auto it = g_tunes.find(bucket_of(vol, cb, K, dt));
+    return it == g_tunes.end() ? default_tune() : it->second;
+}
+
+int gather_blocks(const Tune& T) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                   cudaSuccess)
+        sms = 152;
+    const int nb = T.adj_mult * sms;
+    return nb < 1 ? 1 : (nb > ADJ_MAX_BLOCKS ? ADJ_MAX_BLOCKS : nb);
 }
 
 // ------------------------------------------------------------ small kernels
@@ -359,18 +443,105 @@ int check_finite(const double* v, int n, const char* name) {
 // Everything up to and including the gradient at st->w: warp, DRR with
 // moments, (A.1) + residual + J, fused adjoint gradient.
 int eval_gradient_pipeline(const void* f0, const void* mean, const void* U, int dt, int K, const float* y,
-                           const Grid& g, const View& V, const Ws& W, int step_setup,
+                           const Grid& g, const View& V, const Ws& W, int step_setup, const Tune& T,
                            cudaStream_t s) {
     WSrc ws{};
     ws.dev = W.st->w;
     ws.phase = &W.st->phase;
     PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, dt, K, ws, g, W.view, W.fpad, W.st->box[0], s));
     PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
-                launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, s));
+                launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, T, s));
     PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, W.view, 1, W.rayt, W.st, W.part_res, s));
     PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
                 launch_adjoint_grad(W.rayt, g, W.view, f0, mean, U, dt, K, step_setup, W.st, W.part_adj, W.adj,
-                                    adjoint_block_cap(), s));
+                                    T.vt, gather_blocks(T), s));
+    return PCAS_OK;
+}
+
+// The host-driven solve (solve_projection) with launch shapes T.
+int solve_host(const void* f0, const void* mean, const void* U, int dtype, int K, const float* y,
+               const pcas_vol* vol, const pcas_cb* cb, const double* w_init, const pcas_params* prm,
+               const Tune& T, double* w_out, pcas_stats* stats, void* ws, size_t ws_bytes, cudaStream_t s) {
+    View V;
+    PCAS_TRY(make_view(vol, cb, prm->step_mm, &V));
+    set_layouts(V, T, cb->angle_rad);
+    Ws W;
+    PCAS_TRY(bind_ws(ws, ws_bytes, vol, cb, K, &W));
+    Grid g = make_grid(vol);
+    const int adj_blocks = gather_blocks(T);
+    PCAS_CUDA(cudaMemsetAsync(W.fpad, 0, W.fpad_bytes + W.fpad4_bytes, s));   // zero halos
+    PCAS_TRY(launch_init(W.st, K, w_init, prm, s));
+    PCAS_TRY(upload_view(W.view, V, s));
+    WSrc wcur{}, wtrial{};
+    wcur.dev = W.st->w;
+    wcur.phase = &W.st->phase;
+    wtrial.dev = W.st->wt[0];
+    wtrial.phase = &W.st->phase;
+    wtrial.nvalid = &W.st->nvalid;
+    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, dtype, K, wcur, g, W.view, W.fpad, W.st->box[0], s));
+    PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
+                launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, T, s));
+    int iters = 0, phase = PH_RUNNING;
+    for (int it = 0; it < prm->max_iter; it++) {
+        PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, W.view, it == 0, W.rayt, W.st, W.part_res, s));
+        PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
+                    launch_adjoint_grad(W.rayt, g, W.view, f0, mean, U, dtype, K, 1, W.st, W.part_adj, W.adj, T.vt,
+                                        adj_blocks, s));
+        // Armijo backtracking over the schedule mu0, beta mu0, ...: the next (up
+        // to four) step sizes that the rule may still try are rendered and
+        // tested in one pass; the device accepts the first that passes, in
+        // order.  The host mirrors the schedule only to size each batch, and
+        // reads one flag per batch.
+        double mu_t = prm->mu0;
+        int t = 0;
+        phase = PH_RUNNING;
+        for (int batch = 0; batch <= prm->max_trials; batch++) {    // each batch tries >= 1 step
+            int nvalid = 0;
+            double m = mu_t;
+            while (nvalid < TRIAL_BATCH && m >= prm->mu_min && t + nvalid < prm->max_trials) {
+                nvalid++;
+                m *= prm->beta;
+            }
+            if (nvalid == 0) {          // nothing left to try: the device has stopped too
+                PCAS_CUDA(cudaMemcpyAsync(&phase, &W.st->phase, sizeof(int), cudaMemcpyDeviceToHost, s));
+                PCAS_CUDA(cudaStreamSynchronize(s));
+                if (phase == PH_RUNNING) phase = PH_STOP;
+                break;
+            }
+            if (nvalid >= 2) {
+                PCAS_LAUNCH(PCAS_K_WARP_BATCH, s, launch_warp_batch(f0, mean, U, dtype, K, W.st, g, W.view, W.fpad4, s));
+                PCAS_LAUNCH(PCAS_K_DRR_BATCH, s,
+                            launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, TRIAL_BATCH,
+                                              W.st, W.part_drr, T, s));
+            } else {
+                PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, dtype, K, wtrial, g, W.view, W.fpad, W.st->box[0], s));
+                PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
+                            launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 1, W.st, W.part_drr, T, s));
+            }
+            PCAS_CUDA(cudaMemcpyAsync(&phase, &W.st->phase, sizeof(int), cudaMemcpyDeviceToHost, s));
+            PCAS_CUDA(cudaStreamSynchronize(s));
+            if (phase != PH_RUNNING) break;
+            t += nvalid;
+            mu_t = m;
+        }
+        if (phase == PH_ACCEPT || phase == PH_STOP) iters++;
+        if (phase != PH_ACCEPT) break;
+    }
+    SolveState h;
+    PCAS_CUDA(cudaMemcpyAsync(&h, W.st, sizeof(h), cudaMemcpyDeviceToHost, s));
+    PCAS_CUDA(cudaStreamSynchronize(s));
+    if (h.phase == PH_SINGULAR) return fail(PCAS_ERR_SINGULAR, "Y^T Y is singular (constant image y)");
+    for (int k = 0; k < K; k++) w_out[k] = h.w[k];
+    if (stats) {
+        stats->iters = iters;
+        stats->evals = h.evals;
+        stats->status = PCAS_OK;
+        stats->J0 = h.J0;
+        stats->J = h.J;
+        stats->a = h.a;
+        stats->b = h.b;
+        stats->mu_last = h.mu;
+    }
     return PCAS_OK;
 }
 
@@ -513,6 +684,8 @@ int cost_grad_typed(const void* f0, const void* mean, const void* U, int dtype, 
     PCAS_TRY(check_finite(w, K, "w"));
     View V;
     PCAS_TRY(make_view(vol, cb, step_mm, &V));
+    const Tune T = tune_for(vol, cb, K, dtype);
+    set_layouts(V, T, cb->angle_rad);
     Ws W;
     PCAS_TRY(bind_ws(ws, ws_bytes, vol, cb, K, &W));
     cudaStream_t s = as_stream(stream);
@@ -520,7 +693,7 @@ int cost_grad_typed(const void* f0, const void* mean, const void* U, int dtype, 
     PCAS_CUDA(cudaMemsetAsync(W.fpad, 0, W.fpad_bytes, s));
     PCAS_TRY(launch_init(W.st, K, w, nullptr, s));
     PCAS_TRY(upload_view(W.view, V, s));
-    PCAS_TRY(eval_gradient_pipeline(f0, mean, U, dtype, K, y, g, V, W, 0, s));
+    PCAS_TRY(eval_gradient_pipeline(f0, mean, U, dtype, K, y, g, V, W, 0, T, s));
     SolveState h;
     PCAS_CUDA(cudaMemcpyAsync(&h, W.st, sizeof(h), cudaMemcpyDeviceToHost, s));
     PCAS_CUDA(cudaStreamSynchronize(s));
@@ -558,6 +731,8 @@ int cost_grad_f0(const float* f0, const float* mean, const float* U, int K, cons
     if (dJdf0 && !dJdw) return fail(PCAS_ERR_INVALID_ARG, "dJdf0 needs dJdw (the gradient passes run together)");
     View V;
     PCAS_TRY(make_view(vol, cb, step_mm, &V));
+    const Tune T = tune_for(vol, cb, K, PCAS_F32);
+    set_layouts(V, T, cb->angle_rad);
     if (!ws) return fail(PCAS_ERR_INVALID_ARG, "workspace is NULL");
     const size_t need = pcas_workspace_bytes_f0(vol, cb, K);
     if (ws_bytes < need) return fail(PCAS_ERR_INVALID_ARG, "workspace too small: %zu < %zu bytes", ws_bytes, need);
@@ -579,12 +754,12 @@ int cost_grad_f0(const float* f0, const float* mean, const float* U, int K, cons
     wsrc.phase = &W.st->phase;
     PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, DT_F32, K, wsrc, g, W.view, W.fpad, W.st->box[0], s));
     PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
-                launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, s));
+                launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, T, s));
     PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, W.view, 1, W.rayt, W.st, W.part_res, s));
     if (dJdw)
         PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
                     launch_adjoint_grad(W.rayt, g, W.view, f0, mean, U, DT_F32, K, 0, W.st, W.part_adj, W.adj,
-                                        adjoint_block_cap(), s));
+                                        T.vt, gather_blocks(T), s));
     if (dJdf0)
         PCAS_LAUNCH(PCAS_K_GRAD_F0, s, launch_grad_f0(W.rayt, g, W.view, mean, U, K, W.st, z, zmax, acc, dJdf0, s));
     SolveState h;
@@ -615,86 +790,8 @@ int solve_projection_typed(const void* f0, const void* mean, const void* U, int 
     if (!(prm->mu0 > 0) || !(prm->alpha >= 0) || !(prm->beta > 0 && prm->beta < 1) ||
         !(prm->mu_min >= 0) || prm->max_iter < 0 || prm->max_trials < 0 || prm->max_trials > 1000)
         return fail(PCAS_ERR_INVALID_ARG, "solver parameters out of range");
-    View V;
-    PCAS_TRY(make_view(vol, cb, prm->step_mm, &V));
-    Ws W;
-    PCAS_TRY(bind_ws(ws, ws_bytes, vol, cb, K, &W));
-    cudaStream_t s = as_stream(stream);
-    Grid g = make_grid(vol);
-    const int adj_cap = adjoint_block_cap();
-    PCAS_CUDA(cudaMemsetAsync(W.fpad, 0, W.fpad_bytes + W.fpad4_bytes, s));   // zero halos
-    PCAS_TRY(launch_init(W.st, K, w_init, prm, s));
-    PCAS_TRY(upload_view(W.view, V, s));
-    WSrc wcur{}, wtrial{};
-    wcur.dev = W.st->w;
-    wcur.phase = &W.st->phase;
-    wtrial.dev = W.st->wt[0];
-    wtrial.phase = &W.st->phase;
-    wtrial.nvalid = &W.st->nvalid;
-    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, dtype, K, wcur, g, W.view, W.fpad, W.st->box[0], s));
-    PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
-                launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, s));
-    int iters = 0, phase = PH_RUNNING;
-    for (int it = 0; it < prm->max_iter; it++) {
-        PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, W.view, it == 0, W.rayt, W.st, W.part_res, s));
-        PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
-                    launch_adjoint_grad(W.rayt, g, W.view, f0, mean, U, dtype, K, 1, W.st, W.part_adj, W.adj, adj_cap, s));
-        // Armijo backtracking over the schedule mu0, beta mu0, ...: the next (up
-        // to four) step sizes that the rule may still try are rendered and
-        // tested in one pass; the device accepts the first that passes, in
-        // order.  The host mirrors the schedule only to size each batch, and
-        // reads one flag per batch.
-        double mu_t = prm->mu0;
-        int t = 0;
-        phase = PH_RUNNING;
-        for (int batch = 0; batch <= prm->max_trials; batch++) {    // each batch tries >= 1 step
-            int nvalid = 0;
-            double m = mu_t;
-            while (nvalid < TRIAL_BATCH && m >= prm->mu_min && t + nvalid < prm->max_trials) {
-                nvalid++;
-                m *= prm->beta;
-            }
-            if (nvalid == 0) {          // nothing left to try: the device has stopped too
-                PCAS_CUDA(cudaMemcpyAsync(&phase, &W.st->phase, sizeof(int), cudaMemcpyDeviceToHost, s));
-                PCAS_CUDA(cudaStreamSynchronize(s));
-                if (phase == PH_RUNNING) phase = PH_STOP;
-                break;
-            }
-            if (nvalid >= 2) {
-                PCAS_LAUNCH(PCAS_K_WARP_BATCH, s, launch_warp_batch(f0, mean, U, dtype, K, W.st, g, W.view, W.fpad4, s));
-                PCAS_LAUNCH(PCAS_K_DRR_BATCH, s,
-                            launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, TRIAL_BATCH,
-                                              W.st, W.part_drr, s));
-            } else {
-                PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, dtype, K, wtrial, g, W.view, W.fpad, W.st->box[0], s));
-                PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
-                            launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 1, W.st, W.part_drr, s));
-            }
-            PCAS_CUDA(cudaMemcpyAsync(&phase, &W.st->phase, sizeof(int), cudaMemcpyDeviceToHost, s));
-            PCAS_CUDA(cudaStreamSynchronize(s));
-            if (phase != PH_RUNNING) break;
-            t += nvalid;
-            mu_t = m;
-        }
-        if (phase == PH_ACCEPT || phase == PH_STOP) iters++;
-        if (phase != PH_ACCEPT) break;
-    }
-    SolveState h;
-    PCAS_CUDA(cudaMemcpyAsync(&h, W.st, sizeof(h), cudaMemcpyDeviceToHost, s));
-    PCAS_CUDA(cudaStreamSynchronize(s));
-    if (h.phase == PH_SINGULAR) return fail(PCAS_ERR_SINGULAR, "Y^T Y is singular (constant image y)");
-    for (int k = 0; k < K; k++) w_out[k] = h.w[k];
-    if (stats) {
-        stats->iters = iters;
-        stats->evals = h.evals;
-        stats->status = PCAS_OK;
-        stats->J0 = h.J0;
-        stats->J = h.J;
-        stats->a = h.a;
-        stats->b = h.b;
-        stats->mu_last = h.mu;
-    }
-    return PCAS_OK;
+    return solve_host(f0, mean, U, dtype, K, y, vol, cb, w_init, prm, tune_for(vol, cb, K, dtype), w_out, stats,
+                      ws, ws_bytes, as_stream(stream));
 }
 
 int solve_projection(const float* f0, const float* mean, const float* U, int K, const float* y,
@@ -703,6 +800,226 @@ int solve_projection(const float* f0, const float* mean, const float* U, int K, 
                      size_t ws_bytes, void* stream) {
     return solve_projection_typed(f0, mean, U, PCAS_F32, K, y, vol, cb, w_init, prm, w_out, stats, ws,
                                   ws_bytes, stream);
+}
+
+// ------------------------------------------------------------- autotuner
+}  // extern "C"
+
+namespace {
+
+pcas_tuning to_public(const Tune& T) {
+    pcas_tuning t;
+    t.ray_lw1 = T.lw1; t.ray_lw4 = T.lw4; t.chunk = T.chunk; t.voxel_tile = T.vt; t.gather_per_sm = T.adj_mult;
+    for (int b = 0; b < NBIN; b++) { t.swap1[b] = T.swap1[b]; t.swap4[b] = T.swap4[b]; }
+    return t;
+}
+
+int from_public(const pcas_tuning* t, Tune* T) {
+    if (!t) return fail(PCAS_ERR_INVALID_ARG, "tuning is NULL");
+    if (t->ray_lw1 < 2 || t->ray_lw1 > 4 || t->ray_lw4 < 2 || t->ray_lw4 > 4 || t->chunk < 2 || t->chunk > 64 ||
+        (t->chunk & 1) || t->voxel_tile < 0 || t->voxel_tile >= NVOXTILE || t->gather_per_sm < 1 ||
+        t->gather_per_sm > 26)
+        return fail(PCAS_ERR_INVALID_ARG, "tuning field out of range");
+    for (int b = 0; b < NBIN; b++)
+        if (t->swap1[b] > 1 || t->swap4[b] > 1) return fail(PCAS_ERR_INVALID_ARG, "layout flags must be 0 or 1");
+    T->lw1 = t->ray_lw1; T->lw4 = t->ray_lw4; T->chunk = t->chunk; T->vt = t->voxel_tile;
+    T->adj_mult = t->gather_per_sm;
+    for (int b = 0; b < NBIN; b++) { T->swap1[b] = t->swap1[b]; T->swap4[b] = t->swap4[b]; }
+    return PCAS_OK;
+}
+
+// Runs one trial solve with shapes X at the centre angle of bin b and returns
+// the mean event time per launch of each kernel class (0 where none ran).
+struct Trial {
+    const void *f0, *mean, *U;
+    int dtype, K;
+    const float* y;
+    const pcas_vol* vol;
+    const pcas_cb* cb;
+    pcas_params prm;
+    double w0[PCAS_KMAX];
+    void* ws;
+    size_t ws_bytes;
+    cudaStream_t s;
+    LocalTimer* timer;
+
+    int run(const Tune& X, int b, double avg[PCAS_K_COUNT]) {
+        for (int k = 0; k < PCAS_K_COUNT; k++) avg[k] = 0.0;
+        pcas_cb c = *cb;
+        c.angle_rad = b * (M_PI / NBIN);
+        double w[PCAS_KMAX];
+        pcas_stats st;
+        timer->used = 0;
+        t_local = timer;
+        const int rc = solve_host(f0, mean, U, dtype, K, y, vol, &c, w0, &prm, X, w, &st, ws, ws_bytes, s);
+        t_local = nullptr;
+        if (rc != PCAS_OK) return rc;
+        PCAS_CUDA(cudaStreamSynchronize(s));
+        double tot[PCAS_K_COUNT] = {0};
+        int n[PCAS_K_COUNT] = {0};
+        for (int i = 0; i < timer->used; i++) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, timer->ev[2 * i], timer->ev[2 * i + 1]) != cudaSuccess) continue;
+            tot[timer->kind[i]] += ms;
+            n[timer->kind[i]]++;
+        }
+        for (int k = 0; k < PCAS_K_COUNT; k++) avg[k] = n[k] ? tot[k] / n[k] : 0.0;
+        return PCAS_OK;
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+int pcas_autotune(const void* f0, const void* mean, const void* U, int dtype, int K, const pcas_vol* vol,
+                  const pcas_cb* cb, const pcas_params* params, const double* w_init, const float* y, void* ws,
+                  size_t ws_bytes, pcas_tuning* out, void* stream) {
+    PCAS_TRY(check_vol(vol));
+    PCAS_TRY(check_model(mean, U, K));
+    PCAS_TRY(check_dtype(dtype));
+    PCAS_TRY(check_ptr(f0, "f0"));
+    PCAS_TRY(check_ptr(y, "y"));
+    PCAS_TRY(check_ptr(params, "params"));
+    if (!cb) return fail(PCAS_ERR_INVALID_ARG, "cb is NULL");
+    if (w_init) PCAS_TRY(check_finite(w_init, K, "w_init"));
+    {
+        View V;
+        PCAS_TRY(make_view(vol, cb, params->step_mm, &V));
+        Ws W;
+        PCAS_TRY(bind_ws(ws, ws_bytes, vol, cb, K, &W));
+    }
+    Trial tr;
+    tr.f0 = f0; tr.mean = mean; tr.U = U; tr.dtype = dtype; tr.K = K; tr.y = y; tr.vol = vol; tr.cb = cb;
+    tr.prm = *params;
+    if (tr.prm.max_iter > 3) tr.prm.max_iter = 3;
+    for (int k = 0; k < PCAS_KMAX; k++) tr.w0[k] = (w_init && k < K) ? w_init[k] : 0.0;
+    tr.ws = ws;
+    tr.ws_bytes = ws_bytes;
+    tr.s = as_stream(stream);
+    LocalTimer* timer = new LocalTimer();
+    tr.timer = timer;
+    Tune best = tune_for(vol, cb, K, dtype);
+    double a[PCAS_K_COUNT];
+    int rc = PCAS_OK;
+    bool ok_bin[NBIN];
+    // 1. per angle bin, the layout of each solver volume: one-volume kernels
+    //    (warp + projector) and four-candidate kernels, timed together
+    for (int b = 0; b < NBIN && rc == PCAS_OK; b++) {
+        double t1[2] = {0, 0}, t4[2] = {0, 0};
+        ok_bin[b] = true;
+        for (int sw = 0; sw < 2 && ok_bin[b]; sw++) {
+            Tune X = best;
+            X.swap1[b] = X.swap4[b] = (unsigned char)sw;
+            const int r = tr.run(X, b, a);
+            if (r == PCAS_ERR_INVALID_ARG) { ok_bin[b] = false; break; }   // view invalid at this angle
+            if (r != PCAS_OK) { rc = r; break; }
+            t1[sw] = a[PCAS_K_WARP_PCA] + a[PCAS_K_DRR_SOLVER];
+            t4[sw] = a[PCAS_K_WARP_BATCH] + a[PCAS_K_DRR_BATCH];
+        }
+        if (rc != PCAS_OK || !ok_bin[b]) continue;
+        best.swap1[b] = t1[1] < t1[0] ? 1 : 0;
+        if (t4[0] > 0 && t4[1] > 0) best.swap4[b] = t4[1] < t4[0] ? 1 : 0;
+    }
+    const int probe[4] = {0, 2, 4, 6};
+    auto sweep = [&](auto apply, const int* cands, int ncand, const int* kinds, int nkinds, const int* bins,
+                     int nbins, int* choice) -> int {
+        double bestt = 0.0;
+        for (int c = 0; c < ncand; c++) {
+            Tune X = best;
+            apply(X, cands[c]);
+            double t = 0.0;
+            int used = 0;
+            for (int q = 0; q < nbins; q++) {
+                if (!ok_bin[bins[q]]) continue;
+                const int r = tr.run(X, bins[q], a);
+                if (r != PCAS_OK) return r;
+                for (int k = 0; k < nkinds; k++) t += a[kinds[k]];
+                used++;
+            }
+            if (used && (c == 0 || t < bestt)) {
+                bestt = t;
+                *choice = cands[c];
+            }
+        }
+        return PCAS_OK;
+    };
+    // 2. warp patch widths of the two projectors (each judged by its own kernel)
+    if (rc == PCAS_OK) {
+        double t1best = 0.0, t4best = 0.0;
+        int c1 = best.lw1, c4 = best.lw4;
+        for (int lw = 2; lw <= 4 && rc == PCAS_OK; lw++) {
+            Tune X = best;
+            X.lw1 = X.lw4 = lw;
+            double t1 = 0.0, t4 = 0.0;
+            int used = 0;
+            for (int q = 0; q < 4 && rc == PCAS_OK; q++) {
+                if (!ok_bin[probe[q]]) continue;
+                rc = tr.run(X, probe[q], a);
+                t1 += a[PCAS_K_DRR_SOLVER];
+                t4 += a[PCAS_K_DRR_BATCH];
+                used++;
+            }
+            if (rc != PCAS_OK || !used) continue;
+            if (lw == 2 || t1 < t1best) { t1best = t1; c1 = lw; }
+            if (lw == 2 || t4 < t4best) { t4best = t4; c4 = lw; }
+        }
+        best.lw1 = c1;
+        best.lw4 = c4;
+    }
+    // 3. chunk of the four-candidate projector
+    if (rc == PCAS_OK) {
+        const int ch[3] = {12, 16, 24};
+        const int k4[1] = {PCAS_K_DRR_BATCH};
+        int c = best.chunk;
+        rc = sweep([](Tune& X, int v) { X.chunk = v; }, ch, 3, k4, 1, probe, 4, &c);
+        best.chunk = c;
+    }
+    // 4. voxel tile and gather size of the gradient pass
+    if (rc == PCAS_OK) {
+        const int vts[NVOXTILE] = {0, 1, 2, 3, 4, 5}, gs[3] = {4, 8, 16};
+        const int ka[1] = {PCAS_K_ADJ_GRAD};
+        const int bins2[2] = {0, 4};
+        int c = best.vt;
+        rc = sweep([](Tune& X, int v) { X.vt = v; }, vts, NVOXTILE, ka, 1, bins2, 2, &c);
+        best.vt = c;
+        int g = best.adj_mult;
+        if (rc == PCAS_OK) rc = sweep([](Tune& X, int v) { X.adj_mult = v; }, gs, 3, ka, 1, bins2, 2, &g);
+        best.adj_mult = g;
+    }
+    for (int i = 0; i < timer->created; i++) cudaEventDestroy(timer->ev[i]);
+    delete timer;
+    if (rc != PCAS_OK) return rc;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        g_tunes[bucket_of(vol, cb, K, dtype)] = best;
+    }
+    if (out) *out = to_public(best);
+    return PCAS_OK;
+}
+
+int pcas_tuning_get(const pcas_vol* vol, const pcas_cb* cb, int K, int dtype, pcas_tuning* out) {
+    PCAS_TRY(check_vol(vol));
+    PCAS_TRY(check_ptr(out, "out"));
+    if (!cb) return fail(PCAS_ERR_INVALID_ARG, "cb is NULL");
+    *out = to_public(tune_for(vol, cb, K, dtype));
+    return PCAS_OK;
+}
+
+int pcas_tuning_set(const pcas_vol* vol, const pcas_cb* cb, int K, int dtype, const pcas_tuning* t) {
+    PCAS_TRY(check_vol(vol));
+    if (!cb) return fail(PCAS_ERR_INVALID_ARG, "cb is NULL");
+    Tune T;
+    PCAS_TRY(from_public(t, &T));
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    g_tunes[bucket_of(vol, cb, K, dtype)] = T;
+    return PCAS_OK;
+}
+
+int pcas_tuning_clear(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    g_tunes.clear();
+    return PCAS_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -980,7 +1297,8 @@ struct pcas_solver_s {
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     View view0;           // geometry at creation (grid sizes)
-    int layout;           // xy_swap of the last staged view; -1: buffers all zero
+    Tune tune;            // launch shapes of the size bucket at creation (captured)
+    int layout;           // swap1 | swap4 << 1 of the last staged view; -1: buffers all zero
 };
 
 struct pcas_batch_s {
@@ -1017,7 +1335,7 @@ int capture_solve(pcas_solver s, cudaGraph_t graph, cudaStream_t cs, const float
     wtrial.dev = W.st->wt[0];
     wtrial.nvalid = &W.st->nvalid;
     PCAS_G(launch_warp_pca(s->f0, s->mean, s->U, s->dtype, s->K, wcur, g, W.view, W.fpad, W.st->box[0], cs));
-    PCAS_G(launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, s->y, W.pbuf, 0, W.st, W.part_drr, cs));
+    PCAS_G(launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, s->y, W.pbuf, 0, W.st, W.part_drr, s->tune, cs));
     k_ctrl_start<<<1, 1, 0, cs>>>(W.st, s->h_outer);
     PCAS_G(cudaGetLastError());
     cudaGraph_t outer_body;
@@ -1029,7 +1347,7 @@ int capture_solve(pcas_solver s, cudaGraph_t graph, cudaStream_t cs, const float
     PCAS_G(cudaStreamBeginCaptureToGraph(cs, outer_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     PCAS_G(launch_resid(W.pbuf, s->y, V, W.view, -1, W.rayt, W.st, W.part_res, cs));
     PCAS_G(launch_adjoint_grad(W.rayt, g, W.view, s->f0, s->mean, s->U, s->dtype, s->K, 1, W.st, W.part_adj,
-                               W.adj, adjoint_block_cap(), cs));
+                               W.adj, s->tune.vt, gather_blocks(s->tune), cs));
     k_ctrl_batches<<<1, 1, 0, cs>>>(W.st, s->h_inner);
     PCAS_G(cudaGetLastError());
     cudaGraph_t inner_body;
@@ -1040,9 +1358,10 @@ int capture_solve(pcas_solver s, cudaGraph_t graph, cudaStream_t cs, const float
     // one candidate batch: the four-volume pair or the one-volume pair runs
     PCAS_G(cudaStreamBeginCaptureToGraph(cs, inner_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     PCAS_G(launch_warp_batch(s->f0, s->mean, s->U, s->dtype, s->K, W.st, g, W.view, W.fpad4, cs));
-    PCAS_G(launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, s->y, W.pbuf, TRIAL_BATCH, W.st, W.part_drr, cs));
+    PCAS_G(launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, s->y, W.pbuf, TRIAL_BATCH, W.st, W.part_drr,
+                             s->tune, cs));
     PCAS_G(launch_warp_pca(s->f0, s->mean, s->U, s->dtype, s->K, wtrial, g, W.view, W.fpad, W.st->box[0], cs));
-    PCAS_G(launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, s->y, W.pbuf, 1, W.st, W.part_drr, cs));
+    PCAS_G(launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, s->y, W.pbuf, 1, W.st, W.part_drr, s->tune, cs));
     k_ctrl_batch_end<<<1, 1, 0, cs>>>(W.st, s->h_inner);
     PCAS_G(cudaGetLastError());
     PCAS_G(cudaStreamEndCapture(cs, &done));
@@ -1060,9 +1379,11 @@ int solver_stage(pcas_solver s, double angle_rad, double off_u, double off_v, co
     View V;
     PCAS_TRY(make_view(&s->vol, &cb, s->prm.step_mm, &V));
     PCAS_TRY(check_finite(w_init, s->K, "w_init"));
-    if (s->layout >= 0 && s->layout != V.xy_swap)   // the other layout's voxels lie on this one's halo
+    set_layouts(V, s->tune, angle_rad);
+    const int lay = V.swap1 | V.swap4 << 1;
+    if (s->layout >= 0 && s->layout != lay)   // the other layout's voxels lie on this one's halo
         PCAS_CUDA(cudaMemsetAsync(s->W.fpad, 0, s->W.fpad_bytes + s->W.fpad4_bytes, st));
-    s->layout = V.xy_swap;
+    s->layout = lay;
     *s->h_view = V;
     InitBlock ib = {};
     for (int k = 0; k < s->K; k++) ib.w[k] = w_init[k];
@@ -1131,6 +1452,8 @@ int pcas_solver_create(pcas_solver* out, const void* f0, const void* mean, const
     pcas_solver s = new pcas_solver_s();
     s->vol = *vol; s->cb = *cb; s->prm = *prm; s->K = K; s->dtype = dtype;
     s->f0 = f0; s->mean = mean; s->U = U; s->view0 = V; s->layout = -1;
+    s->tune = tune_for(vol, cb, K, dtype);
+    set_layouts(s->view0, s->tune, cb->angle_rad);
     int rc = bind_ws(ws, base, vol, cb, K, &s->W);
     if (rc != PCAS_OK) { solver_free(s); return rc; }
     char* extra = static_cast<char*>(ws) + base;
@@ -1152,7 +1475,7 @@ int pcas_solver_create(pcas_solver* out, const void* f0, const void* mean, const
         solver_free(s);
         return fail(PCAS_ERR_CUDA, "solver set-up failed: %s", cudaGetErrorString(e));
     }
-    *s->h_view = V;
+    *s->h_view = s->view0;
     rc = capture_solve(s, s->graph, cs, nullptr);
     cudaStreamDestroy(cs);
     if (rc != PCAS_OK) { solver_free(s); return rc; }

@@ -24,7 +24,8 @@ struct View {
     float u0, du, v0, dv;    // detector coordinates of pixel centres, mm
     int nu, nv;
     float step;              // ray-march step, mm
-    int xy_swap;             // solver volumes stored with x and y exchanged (|sin a| > |cos a|)
+    int swap1, swap4;        // layout of the one-volume / four-candidate solver volumes:
+                             // 1 = x and y exchanged (see solver_pad), chosen per angle
 };
 
 struct Grid {
@@ -53,13 +54,12 @@ __host__ __device__ inline long pad_index(const Pad& pd, int i, int j, int k) {
     return ((long)(k + 2) * pd.pny + (j + 2)) * pd.px + (i + 4);
 }
 
-// Solver volume layout.  A ray crosses voxels mostly along its dominant
-// direction, and a warp's rays are neighbours along the detector u axis,
-// which is world x at gantry 0 and world y at 90 degrees.  For views with
-// |sin a| > |cos a| the warp kernels store the solver volumes with x and y
-// exchanged (y fastest), so that u-neighbouring rays read neighbouring
-// addresses at every angle; the projector then marches the mirrored
-// geometry: the same sample points with their x and y coordinates exchanged.
+// Solver volume layout.  A warp's rays are neighbours along the detector u
+// axis, which is world x at gantry 0 and world y at 90 degrees, so which
+// voxels they read together depends on the angle.  Each solver volume is
+// stored either x fastest or with x and y exchanged (y fastest), chosen per
+// 22.5-degree bin of the angle (Tune); the projector then marches the
+// mirrored geometry: the same sample points with x and y exchanged.
 __host__ __device__ inline Pad solver_pad(int nx, int ny, int nz, int xy_swap) {
     return xy_swap ? make_pad(ny, nx, nz) : make_pad(nx, ny, nz);
 }
@@ -242,10 +242,10 @@ __device__ __forceinline__ float4 tri_padded4(const float4* __restrict__ f, cons
 template <typename X>
 __device__ __forceinline__ void swap_xy(X& a, X& b) { X t = a; a = b; b = t; }
 
-// The view, grid and layout of the solver volumes in the frame they are stored
-// in (see solver_pad): a no-op unless V.xy_swap is set.
-__device__ __forceinline__ void solver_frame(View& V, Grid& g, Pad& pd) {
-    if (V.xy_swap) {
+// The view, grid and layout of a solver volume in the frame it is stored in
+// (see solver_pad): a no-op unless swap is set.
+__device__ __forceinline__ void solver_frame(View& V, Grid& g, Pad& pd, int swap) {
+    if (swap) {
         swap_xy(V.Q0.x, V.Q0.y); swap_xy(V.A.x, V.A.y); swap_xy(V.Bu.x, V.Bu.y); swap_xy(V.Bv.x, V.Bv.y);
         swap_xy(V.EW.x, V.EW.y); swap_xy(V.EU.x, V.EU.y); swap_xy(V.EV.x, V.EV.y);
         swap_xy(g.nx, g.ny); swap_xy(g.inv_sx, g.inv_sy);
@@ -365,6 +365,59 @@ __device__ bool block_reduce_last(const float (&v)[NV], Reduce red, unsigned int
     return true;
 }
 
+// ------------------------------------------------------------ launch shapes
+// Launch shapes of the solver kernels, chosen per size bucket: the defaults
+// below, or the ones pcas_autotune measured fastest for the bucket.
+enum { NBIN = 8 };            // 22.5-degree bins of the gantry angle modulo 180 degrees
+struct Tune {
+    int lw1, lw4;             // log2 of a warp's patch width in pixels along u (2..4);
+                              // the patch is (1 << lw) x (32 >> lw), four warps per block
+                              // stacked along v; 1: one-volume, 4: four-candidate projector
+    int chunk;                // sample indices per staged chunk, four-candidate projector
+    int vt;                   // voxel tile of the gradient pass (vox_tile)
+    int adj_mult;             // gather blocks = adj_mult x the resident blocks of 256 threads
+    unsigned char swap1[NBIN], swap4[NBIN];   // volume layouts per angle bin (solver_pad)
+};
+
+// Voxel tiles of the gradient pass (256 voxels): log2 of the x, y, z extents.
+enum { NVOXTILE = 6 };
+__host__ __device__ inline void vox_tile(int vt, int& lx, int& ly, int& lz) {
+    switch (vt) {
+        case 1: lx = 4; ly = 2; lz = 2; break;   // 16 x 4 x 4
+        case 2: lx = 5; ly = 2; lz = 1; break;   // 32 x 4 x 2
+        case 3: lx = 4; ly = 3; lz = 1; break;   // 16 x 8 x 2
+        case 4: lx = 5; ly = 3; lz = 0; break;   // 32 x 8 x 1
+        case 5: lx = 6; ly = 2; lz = 0; break;   // 64 x 4 x 1
+        default: lx = 3; ly = 3; lz = 2; break;  // 8 x 8 x 4
+    }
+}
+inline long adj_tiles(int nx, int ny, int nz, int vt) {
+    int lx, ly, lz;
+    vox_tile(vt, lx, ly, lz);
+    return (long)((nx + (1 << lx) - 1) >> lx) * ((ny + (1 << ly) - 1) >> ly) * ((nz + (1 << lz) - 1) >> lz);
+}
+inline long adj_tiles_max(int nx, int ny, int nz) {
+    long m = 0;
+    for (int vt = 0; vt < NVOXTILE; vt++) {
+        const long t = adj_tiles(nx, ny, nz, vt);
+        m = t > m ? t : m;
+    }
+    return m;
+}
+
+// Blocks of the solver projector for a patch width of 1 << lw pixels
+// (blocks of 128 rays: (1 << lw) x (128 >> lw) pixels).
+inline unsigned drr_blocks_x(int nu, int lw) { return (unsigned)((nu + (1 << lw) - 1) >> lw); }
+inline unsigned drr_blocks_y(int nv, int lw) { return (unsigned)((nv + (128 >> lw) - 1) / (128 >> lw)); }
+inline unsigned drr_blocks(int nu, int nv) {           // the largest grid over lw = 2..4
+    unsigned m = 0;
+    for (int lw = 2; lw <= 4; lw++) {
+        const unsigned b = drr_blocks_x(nu, lw) * drr_blocks_y(nv, lw);
+        m = b > m ? b : m;
+    }
+    return m;
+}
+
 // ------------------------------------------------------- launch interfaces
 struct WSrc {                 // where a PCA-model kernel takes w from
     float w[PCAS_KMAX];       // used when dev is null
@@ -381,8 +434,8 @@ cudaError_t launch_pca_dvf(const void* mean, const void* U, int dt, int K, const
 cudaError_t launch_warp_dvf(const void* f0, int dt, const float* dvf, Grid g, float* f, cudaStream_t s);
 // Solver warp: S = 1 writes f(w_src) to the scalar zero-halo buffer; S = 4
 // writes the four candidate volumes st->wt[0..3] interleaved (float4).
-// Vd (device, may be null): its xy_swap selects the layout (solver_pad); the
-// bounding box is recorded in the same frame.
+// Vd (device, may be null): its swap1 (one volume) or swap4 (four candidates)
+// selects the layout (solver_pad); the bounding box is recorded in the same frame.
 cudaError_t launch_warp_pca(const void* f0, const void* mean, const void* U, int dt, int K, WSrc w,
                             Grid g, const View* Vd, float* fpad, int* box, cudaStream_t s);
 cudaError_t launch_warp_batch(const void* f0, const void* mean, const void* U, int dt, int K,
@@ -403,23 +456,22 @@ cudaError_t launch_drr_siddon(const float* f, const SidView& V, float* p, cudaSt
 // memory (read by the kernels, so captured launches stay view-independent).
 cudaError_t launch_drr_solver(const float* fpad, const float4* fpad4, Grid g,
                               const View& Vh, const View* Vd, const float* y, float* pbuf, int mode,
-                              SolveState* st, double* part, cudaStream_t s);
+                              SolveState* st, double* part, const Tune& T, cudaStream_t s);
 cudaError_t launch_resid(const float* pbuf, const float* y, const View& Vh, const View* Vd, int first,
                          float4* rayt, SolveState* st, double* part, cudaStream_t s);
 cudaError_t launch_adjoint_plain(const float* img, Grid g, const View& V, float* gout,
                                  cudaStream_t s);
 // Scratch of the gradient pass: compacted voxels with a non-zero warp
-// Jacobian (index and h_k, per 8x8x4 tile) and the tile counts / offsets.
+// Jacobian (index and h_k, per voxel tile of 256) and the tile counts / offsets.
 struct AdjScratch {
     int* act_idx;       // ntiles * 256
     float* act_h;       // K * ntiles * 256
     int* tile_count;    // ntiles
     int* tile_off;      // ntiles + 1
 };
-inline long adj_tiles(int nx, int ny, int nz) { return (long)((nx + 7) / 8) * ((ny + 7) / 8) * ((nz + 3) / 4); }
 cudaError_t launch_adjoint_grad(const float4* rayt, Grid g, const View* V, const void* f0,
                                 const void* mean, const void* U, int dt, int K, int step_setup,
-                                SolveState* st, double* part, const AdjScratch& as, int max_blocks,
+                                SolveState* st, double* part, const AdjScratch& as, int vt, int max_blocks,
                                 cudaStream_t s);
 // dJ/df0 = W^T (2 P^T r): z (N floats) and acc (N 64-bit) are scratch,
 // zmax_bits one word; out (N floats) receives the gradient.
@@ -431,7 +483,6 @@ cudaError_t launch_localize(const float* mean, const float* U, int K, const doub
                             int max_iter, double tol, double* out, cudaStream_t s);
 
 // Number of partial slots each solver kernel needs (sizes the workspace).
-inline unsigned drr_blocks(int nu, int nv) { return (unsigned)((nu + 7) / 8) * ((nv + 15) / 16); }
 enum { DRR_PART_VALS = 4 * TRIAL_BATCH + 2 };   // per-volume Sp, Syp, Spp, Srr + Sy, Syy
 inline unsigned resid_blocks(int nu, int nv) { return (unsigned)(((long)nu * nv + 255) / 256); }
 enum { ADJ_MAX_BLOCKS = 4096 };

@@ -108,7 +108,7 @@ k_warp_pca(const T* __restrict__ f0, const T* __restrict__ mean,
            float* __restrict__ fpad, int* __restrict__ box_out) {
     if (ws.phase && *ws.phase >= PH_STOP) return;
     if (ws.nvalid && *ws.nvalid != 1) return;
-    const int swp = Vp ? Vp->xy_swap : 0;
+    const int swp = Vp ? Vp->swap1 : 0;
     const Pad pd = solver_pad(g.nx, g.ny, g.nz, swp);
     __shared__ float s_w[PCAS_KMAX];
     if (threadIdx.x < PCAS_KMAX) {
@@ -181,7 +181,7 @@ k_warp_batch(const T* __restrict__ f0, const T* __restrict__ mean,
              const T* __restrict__ U, int K, const SolveState* st, Grid g, const View* __restrict__ Vp,
              float4* __restrict__ fpad4, int* __restrict__ box_out) {
     if (st->phase >= PH_STOP || st->nvalid < 2) return;
-    const int swp = Vp ? Vp->xy_swap : 0;
+    const int swp = Vp ? Vp->swap4 : 0;
     const Pad pd = solver_pad(g.nx, g.ny, g.nz, swp);
     __shared__ float s_w[TRIAL_BATCH][PCAS_KMAX];
     if (threadIdx.x < TRIAL_BATCH * PCAS_KMAX) {

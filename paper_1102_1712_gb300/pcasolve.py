@@ -97,6 +97,11 @@ _SIGS = {
                                     C.c_int, _P]),
     "pcas_batch_solve": (C.c_int, [C.c_void_p, _D, _D, _D, C.POINTER(Stats), _P]),
     "pcas_batch_destroy": (C.c_int, [C.c_void_p]),
+    "pcas_autotune": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.POINTER(Vol), C.POINTER(CB), C.POINTER(Params),
+                                _D, _P, _P, C.c_size_t, _P, _P]),
+    "pcas_tuning_get": (C.c_int, [C.POINTER(Vol), C.POINTER(CB), C.c_int, C.c_int, _P]),
+    "pcas_tuning_set": (C.c_int, [C.POINTER(Vol), C.POINTER(CB), C.c_int, C.c_int, _P]),
+    "pcas_tuning_clear": (C.c_int, []),
     "pcas_profile": (C.c_int, [C.c_int]),
     "pcas_profile_read": (C.c_int, [C.c_int, C.POINTER(C.c_longlong), _D]),
 }
@@ -500,6 +505,62 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Tuning(C.Structure):
+    """pcas_tuning: launch shapes of one size bucket (include/pcasolve.h)."""
+    _fields_ = [("ray_lw1", C.c_int), ("ray_lw4", C.c_int), ("chunk", C.c_int), ("voxel_tile", C.c_int),
+                ("gather_per_sm", C.c_int), ("swap1", C.c_ubyte * 8), ("swap4", C.c_ubyte * 8)]
+
+    def as_dict(self):
+        return {"ray_lw1": self.ray_lw1, "ray_lw4": self.ray_lw4, "chunk": self.chunk,
+                "voxel_tile": self.voxel_tile, "gather_per_sm": self.gather_per_sm,
+                "swap1": list(self.swap1), "swap4": list(self.swap4)}
+
+
+def _tuning_struct(d):
+    t = Tuning()
+    for k in ("ray_lw1", "ray_lw4", "chunk", "voxel_tile", "gather_per_sm"):
+        setattr(t, k, int(d[k]))
+    for k in ("swap1", "swap4"):
+        arr = getattr(t, k)
+        for b, v in enumerate(d[k]):
+            arr[b] = int(v)
+    return t
+
+
+def autotune(f0, mean, U, y, vol, cb, params, w_init=None, ws: Workspace = None, stream=None):
+    """Measure launch shapes on this problem and store the fastest for its size
+    bucket (synchronous, about 60 short trial solves).  Returns the entry."""
+    K = _K(U, vol)
+    N = _nvox(vol)
+    dt = U.dtype
+    g = cb_struct(cb)
+    ws = ws or Workspace(vol, cb, K, device=U.device)
+    w0 = None if w_init is None else _host_d(w_init, K)
+    out = Tuning()
+    _check(lib().pcas_autotune(_dev(f0, "f0", N, dt), _dev(mean, "mean", 3 * N, dt), _dev(U, "U", None, dt),
+                               storage_type(U), K, C.byref(vol_struct(vol)), C.byref(g),
+                               C.byref(params_struct(params)), None if w0 is None else w0.ctypes.data_as(_D),
+                               _dev(y, "y", g.nu * g.nv), ws.ptr, ws.nbytes, C.byref(out), _stream(stream)))
+    return out.as_dict()
+
+
+def tuning_get(vol, cb, K, dtype=None):
+    """The launch shapes in force for this problem's size bucket."""
+    out = Tuning()
+    _check(lib().pcas_tuning_get(C.byref(vol_struct(vol)), C.byref(cb_struct(cb)), int(K),
+                                 F32 if dtype is None else int(dtype), C.byref(out)))
+    return out.as_dict()
+
+
+def tuning_set(vol, cb, K, tuning, dtype=None):
+    _check(lib().pcas_tuning_set(C.byref(vol_struct(vol)), C.byref(cb_struct(cb)), int(K),
+                                 F32 if dtype is None else int(dtype), C.byref(_tuning_struct(tuning))))
+
+
+def tuning_clear():
+    _check(lib().pcas_tuning_clear())
 
 
 def profile(on: bool):

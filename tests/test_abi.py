@@ -152,3 +152,30 @@ def test_lp_fit_and_predict_match_oracle(lib):
     t = np.arange(100) / 10.0
     c = P.lp_fit(np.sin(2 * math.pi * t / 4.0)[:, None], 2)
     assert abs(c[0, 0] - 2 * math.cos(2 * math.pi / 40)) < 1e-9 and abs(c[0, 1] + 1) < 1e-9
+
+
+def test_tuning_table_host_only(lib):
+    """The launch-shape table is host state: set / get / clear and the checks."""
+    vol = S.volume(64, 64, 32, 4.0, 4.0, 4.0)
+    cb = S.cone_beam(128, 96, 3.1, 3.1)
+    P.tuning_clear()
+    d = P.tuning_get(vol, cb, 3)
+    assert d["ray_lw1"] == 3 and d["chunk"] == 16 and d["swap4"] == [0, 0, 0, 1, 1, 1, 0, 0]
+    t = dict(ray_lw1=2, ray_lw4=4, chunk=24, voxel_tile=5, gather_per_sm=2, swap1=[1] * 8, swap4=[0] * 8)
+    P.tuning_set(vol, cb, 3, t)
+    assert P.tuning_get(vol, cb, 3) == t
+    assert P.tuning_get(S.volume(60, 64, 32, 4.0, 4.0, 4.0), cb, 3) == t        # same bucket (x in 33..64)
+    assert P.tuning_get(S.volume(96, 64, 32, 4.0, 4.0, 4.0), cb, 3) == d        # next bucket
+    assert P.tuning_get(vol, cb, 5) == d and P.tuning_get(vol, cb, 3, dtype=P.BF16) == d
+    for bad in (dict(t, ray_lw1=5), dict(t, chunk=13), dict(t, chunk=66), dict(t, voxel_tile=6),
+                dict(t, gather_per_sm=0), dict(t, gather_per_sm=27), dict(t, swap1=[2] + [0] * 7)):
+        with pytest.raises(P.PcasError):
+            P.tuning_set(vol, cb, 3, bad)
+    P.tuning_clear()
+    assert P.tuning_get(vol, cb, 3) == d
+
+
+def test_static_scratch_example_fits(lib):
+    """The size the header quotes as fitting the static scratch does fit."""
+    n = P.workspace_bytes(S.volume(80, 80, 40, 4.0, 4.0, 4.0), S.cone_beam(192, 144, 2.0, 2.0), 3)
+    assert 0 < n <= 16 * 1024 * 1024
