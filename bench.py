@@ -66,6 +66,8 @@ def parse():
                     help="renderer of the measured images: Siddon's exact path (Sec. II.B, no inverse "
                          "crime) or the solver's own trilinear projector")
     ap.add_argument("--angle-deg", type=float, default=90.0, help="gantry angle of the fluoro workload")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shapes instead of tuning the size bucket first")
     return ap.parse_args()
 
 
@@ -267,6 +269,14 @@ def run_ours(args, ws_, rank, local):
     wsp = P.Workspace(vol, view(0.0), K, device=dev)
     torch.cuda.synchronize()
 
+    # launch shapes of this size bucket, measured before anything is timed
+    tune_s, tuning = 0.0, None
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        tuning = P.autotune(tf0, None, tU, ys[0], vol, view(angles[0]), prm, w_init=trace[0], ws=wsp)
+        tune_s = time.perf_counter() - t0
+    else:
+        P.tuning_clear()
     solver = P.Solver(tf0, None, tU, vol, view(0.0), prm, device=dev)
 
     def solve_range(t0, t1, hist, y_of, stats_out, mode="graph"):
@@ -403,6 +413,8 @@ def run_ours(args, ws_, rank, local):
                      "note": "kernel durations from CUDA events in the host-driven pass over the same "
                              "projections (graph launches cannot be bracketed per kernel)"},
         "host_driven": {"value": round(K_ / (ms_host / 1e3), 3), "ms_per_step": round(ms_host / K_, 4)},
+        "launch_shapes": {"autotuned": tuning is not None, "tune_s": round(tune_s, 2),
+                          "entry": tuning or P.tuning_get(vol, view(0.0), K)},
         "kernels": kernels,
         "gpu_launches": launches,
         "clocks": clocks,
@@ -535,6 +547,8 @@ def run_precision(args, local):
     for name, dt in [("float32", torch.float32), ("bfloat16", torch.bfloat16), ("float16", torch.float16)]:
         sf0, sU = tf0.to(dt), tU.to(dt)
         hist = []
+        if not args.no_autotune:
+            P.autotune(sf0, None, sU, ys[0], vol, views[0], prm, w_init=trace[0], ws=wsp)
 
         def solve(t, rec):
             w0 = np.zeros(K) if t == 0 else hist[-1] if t == 1 else P.lp_predict(np.stack([hist[-1], hist[-2]]), c_lp)
@@ -638,7 +652,20 @@ def run_batch(args, local):
         sigma = W["noise"] * float(p.abs().max())
         pb["y"] = p + torch.from_numpy(S.gaussian_noise(M, sigma, seed=300 + i)).to(dev)
         pb["c_true"], _ = P.localize_tumor(None, pb["U"], pb["w_true"], pb["vol"], pb["c_ref"])
-        pb["prm"] = P.default_params(pb["step"])
+        pb["prm"] = P.default_params(pb["step"], max_iter=20)     # cold starts: 20 iterations, as the tiny case
+    # one autotune per size bucket (volume, detector, K), on its first problem
+    t0 = time.perf_counter()
+    tuned = {}
+    for pb in probs:
+        key = (pb["vol"]["nx"], pb["cb"]["nu"], pb["K"])
+        if key in tuned or args.no_autotune:
+            continue
+        ws_t = P.Workspace(pb["vol"], pb["cb"], pb["K"], device=dev)
+        tuned[key] = P.autotune(pb["f0"], None, pb["U"], pb["y"], pb["vol"], pb["cb"], pb["prm"], ws=ws_t)
+        del ws_t
+    if args.no_autotune:
+        P.tuning_clear()
+    tune_s = time.perf_counter() - t0
     solvers = [P.Solver(pb["f0"], None, pb["U"], pb["vol"], pb["cb"], pb["prm"], device=dev) for pb in probs]
     batch = P.Batch(solvers, ys=[pb["y"] for pb in probs])
     angles = [pb["cb"]["angle"] for pb in probs]
@@ -690,7 +717,7 @@ def run_batch(args, local):
             "config": {"workload": W["name"], "solves_per_step": n,
                        "volumes": "128^2x64 / 192^2x96 / 256^2x128", "K": "3 / 5",
                        "detectors": "256x192 / 512x384 / 768x576 / 1024x768", "start": "w = 0",
-                       "solver": "mu0=0.2 alpha=0.1 beta=0.5 mu_min=0.01 max_iter=10"},
+                       "solver": "mu0=0.2 alpha=0.1 beta=0.5 mu_min=0.01 max_iter=20"},
             "one_after_another": {"host_driven": round(n * reps / (ms_s / 1e3), 3),
                                   "graph_per_solve": round(n * reps / (ms_g / 1e3), 3), "unit": "projections/s"},
             "speedup_vs_host_driven": round(ms_s / ms_b, 3),
@@ -698,6 +725,7 @@ def run_batch(args, local):
                          "max": round(float(errs.max()), 4)},
             "solver": {"iters_mean": round(float(np.mean([s["iters"] for s in sts])), 3),
                        "evals_mean": round(float(np.mean([s["evals"] for s in sts])), 3)},
+            "launch_shapes": {"autotuned_buckets": len(tuned), "tune_s": round(tune_s, 2)},
             "gpu_launches": launches, "clocks": clk.summary()}
 
 
