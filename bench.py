@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--angle-deg", type=float, default=90.0, help="gantry angle of the fluoro workload")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shapes instead of tuning the size bucket first")
+    ap.add_argument("--tuning", default=None,
+                    help="launch shapes of the sequence bucket as JSON (pcas_tuning), instead of tuning")
     return ap.parse_args()
 
 
@@ -271,7 +273,9 @@ def run_ours(args, ws_, rank, local):
 
     # launch shapes of this size bucket, measured before anything is timed
     tune_s, tuning = 0.0, None
-    if not args.no_autotune:
+    if args.tuning:
+        P.tuning_set(vol, view(0.0), K, json.loads(args.tuning))
+    elif not args.no_autotune:
         t0 = time.perf_counter()
         tuning = P.autotune(tf0, None, tU, ys[0], vol, view(angles[0]), prm, w_init=trace[0], ws=wsp)
         tune_s = time.perf_counter() - t0
@@ -413,7 +417,7 @@ def run_ours(args, ws_, rank, local):
                      "note": "kernel durations from CUDA events in the host-driven pass over the same "
                              "projections (graph launches cannot be bracketed per kernel)"},
         "host_driven": {"value": round(K_ / (ms_host / 1e3), 3), "ms_per_step": round(ms_host / K_, 4)},
-        "launch_shapes": {"autotuned": tuning is not None, "tune_s": round(tune_s, 2),
+        "launch_shapes": {"autotuned": tuning is not None, "given": bool(args.tuning), "tune_s": round(tune_s, 2),
                           "entry": tuning or P.tuning_get(vol, view(0.0), K)},
         "kernels": kernels,
         "gpu_launches": launches,

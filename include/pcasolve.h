@@ -276,34 +276,37 @@ int lp_predict(const double* hist, const double* c, int K, int L, double* w0);
  * Launch shapes of the solver kernels, kept per size bucket (volume extents
  * in steps of 32, 32, 16 voxels, detector extents in steps of 64 pixels, K,
  * storage type).  No counterpart in the paper; they change speed only.
- *   ray_lw1, ray_lw4  log2 of a warp's patch width on the detector (2..4):
- *                     (1 << lw) x (32 >> lw) pixels, for the one-volume and
- *                     the four-candidate projector
- *   chunk             sample indices per shared-memory chunk of the
- *                     four-candidate projector (even, 2..64)
+ *   ray_lw1           log2 of a warp's patch width on the detector (2..4) of
+ *                     the one-volume projector: (1 << lw) x (32 >> lw) pixels
+ *   chunk1            sample indices per shared-memory chunk of the one-volume
+ *                     projector (even, 0..128; 0 = no staging, reads via L1)
  *   voxel_tile        voxel tile of the gradient pass: 0 = 8x8x4, 1 = 16x4x4,
  *                     2 = 32x4x2, 3 = 16x8x2, 4 = 32x8x1, 5 = 64x4x1
  *   gather_per_sm     blocks of the gradient gather per SM (1..26)
- *   swap1, swap4      layout of the one-volume / four-candidate solver
- *                     volumes per 22.5-degree bin of the gantry angle modulo
- *                     180 degrees (bin b centred on 22.5 b): 0 = x fastest,
- *                     1 = y fastest
- * Every call takes the entry of its bucket, or the defaults (3, 3, 16, 0, 8,
- * y fastest in bins 3..5) when there is none; a device-driven solver takes
- * the entry in force when it is created.  Other shapes reorder floating-point
- * sums: results can differ by rounding between shapes, and are reproducible
- * for a fixed table. */
+ * and per 22.5-degree bin of the gantry angle modulo 180 degrees (bin b is
+ * centred on 22.5 b degrees):
+ *   ray_lw4[b]        patch width of the four-candidate projector (2..4)
+ *   chunk[b]          its sample indices per shared-memory chunk (even, 2..64)
+ *   swap1[b], swap4[b]  layout of the one-volume / four-candidate solver
+ *                     volumes: 0 = x fastest, 1 = y fastest
+ * Every call takes the entry of its bucket, or the defaults (3, 0, 0, 8; per
+ * bin 3, 16, y fastest in bins 3..5) when there is none; a device-driven
+ * solver takes the entry in force when it is created (the per-bin shapes
+ * follow the angle of each solve).  Other shapes reorder floating-point sums:
+ * results can differ by rounding between shapes, and are reproducible for a
+ * fixed table. */
 typedef struct {
-    int ray_lw1, ray_lw4, chunk, voxel_tile, gather_per_sm;
-    unsigned char swap1[8], swap4[8];
+    int ray_lw1, chunk1, voxel_tile, gather_per_sm;
+    unsigned char ray_lw4[8], chunk[8], swap1[8], swap4[8];
 } pcas_tuning;
 
 /* Measures shapes on this problem and stores the fastest in its bucket:
  * trial solves (solve_projection with max_iter capped at 3, from w_init, at
- * the centre angle of a bin), every kernel timed with CUDA events; first the
- * two layouts of each bin, then the patch widths, the chunk, the voxel tile
+ * the centre angle of a bin), every kernel timed with CUDA events: per bin
+ * the layouts, then per bin the patch width and chunk of the four-candidate
+ * projector, then the one-volume projector's width and chunk, the voxel tile
  * and the gather size, each chosen by the time of the kernels it drives
- * (about 60 trial solves).  f0, mean, U, y, ws: device, as solve_projection
+ * (about 130 trial solves).  f0, mean, U, y, ws: device, as solve_projection
  * (ws of pcas_workspace_bytes); w_init: host, K doubles or NULL (zeros);
  * out (host, may be NULL) receives the stored entry.  Synchronous.  Bins
  * whose view is invalid (volume not in front of the source) keep their

@@ -175,7 +175,10 @@ int make_view(const pcas_vol* vol, const pcas_cb* cb, double step, View* V) {
     V->nu = cb->nu;
     V->nv = cb->nv;
     V->step = (float)step;
-    V->swap1 = V->swap4 = 0;                // set per launch shape by set_layouts
+    V->swap1 = V->swap4 = 0;                // launch shapes: set_layouts
+    V->lw1 = V->lw4 = 3;
+    V->chunk1 = 0;
+    V->chunk4 = 16;
     return PCAS_OK;
 }
 
@@ -254,17 +257,21 @@ int bind_ws(void* ws, size_t ws_bytes, const pcas_vol* vol, const pcas_cb* cb, i
 }
 
 // ------------------------------------------------------------ launch shapes
-// Default shapes: 8 x 4 warp patches, 16-sample chunks, 8 x 8 x 4 voxel tiles,
+// Default shapes: 8 x 4 warp patches, 16-sample chunks for the four-candidate
+// projector (the one-volume projector marches through L1), 8 x 8 x 4 voxel tiles,
 // eight gather blocks per SM, y-fastest solver volumes for angles near 90
 // (bins 67.5 ... 112.5 degrees).
 Tune default_tune() {
     Tune T;
     T.lw1 = 3;
-    T.lw4 = 3;
-    T.chunk = 16;
+    T.chunk1 = 0;
     T.vt = 0;
     T.adj_mult = 8;
-    for (int b = 0; b < NBIN; b++) T.swap1[b] = T.swap4[b] = (b >= 3 && b <= 5) ? 1 : 0;
+    for (int b = 0; b < NBIN; b++) {
+        T.lw4[b] = 3;
+        T.chunk4[b] = 16;
+        T.swap1[b] = T.swap4[b] = (b >= 3 && b <= 5) ? 1 : 0;
+    }
     return T;
 }
 
@@ -281,6 +288,10 @@ void set_layouts(View& V, const Tune& T, double angle) {
     const int b = angle_bin(angle);
     V.swap1 = T.swap1[b];
     V.swap4 = T.swap4[b];
+    V.lw1 = T.lw1;
+    V.lw4 = T.lw4[b];
+    V.chunk1 = T.chunk1;
+    V.chunk4 = T.chunk4[b];
 }
 
 // Size buckets: volume extents in steps of 32 (x, y) and 16 (z) voxels,
@@ -809,22 +820,26 @@ namespace {
 
 pcas_tuning to_public(const Tune& T) {
     pcas_tuning t;
-    t.ray_lw1 = T.lw1; t.ray_lw4 = T.lw4; t.chunk = T.chunk; t.voxel_tile = T.vt; t.gather_per_sm = T.adj_mult;
-    for (int b = 0; b < NBIN; b++) { t.swap1[b] = T.swap1[b]; t.swap4[b] = T.swap4[b]; }
+    t.ray_lw1 = T.lw1; t.chunk1 = T.chunk1; t.voxel_tile = T.vt; t.gather_per_sm = T.adj_mult;
+    for (int b = 0; b < NBIN; b++) {
+        t.ray_lw4[b] = T.lw4[b]; t.chunk[b] = T.chunk4[b]; t.swap1[b] = T.swap1[b]; t.swap4[b] = T.swap4[b];
+    }
     return t;
 }
 
 int from_public(const pcas_tuning* t, Tune* T) {
     if (!t) return fail(PCAS_ERR_INVALID_ARG, "tuning is NULL");
-    if (t->ray_lw1 < 2 || t->ray_lw1 > 4 || t->ray_lw4 < 2 || t->ray_lw4 > 4 || t->chunk < 2 || t->chunk > 64 ||
-        (t->chunk & 1) || t->voxel_tile < 0 || t->voxel_tile >= NVOXTILE || t->gather_per_sm < 1 ||
-        t->gather_per_sm > 26)
+    if (t->ray_lw1 < 2 || t->ray_lw1 > 4 || t->chunk1 < 0 || t->chunk1 > 128 || (t->chunk1 & 1) ||
+        t->voxel_tile < 0 || t->voxel_tile >= NVOXTILE || t->gather_per_sm < 1 || t->gather_per_sm > 26)
         return fail(PCAS_ERR_INVALID_ARG, "tuning field out of range");
     for (int b = 0; b < NBIN; b++)
-        if (t->swap1[b] > 1 || t->swap4[b] > 1) return fail(PCAS_ERR_INVALID_ARG, "layout flags must be 0 or 1");
-    T->lw1 = t->ray_lw1; T->lw4 = t->ray_lw4; T->chunk = t->chunk; T->vt = t->voxel_tile;
-    T->adj_mult = t->gather_per_sm;
-    for (int b = 0; b < NBIN; b++) { T->swap1[b] = t->swap1[b]; T->swap4[b] = t->swap4[b]; }
+        if (t->ray_lw4[b] < 2 || t->ray_lw4[b] > 4 || t->chunk[b] < 2 || t->chunk[b] > 64 || (t->chunk[b] & 1) ||
+            t->swap1[b] > 1 || t->swap4[b] > 1)
+            return fail(PCAS_ERR_INVALID_ARG, "tuning field of angle bin %d out of range", b);
+    T->lw1 = t->ray_lw1; T->chunk1 = t->chunk1; T->vt = t->voxel_tile; T->adj_mult = t->gather_per_sm;
+    for (int b = 0; b < NBIN; b++) {
+        T->lw4[b] = t->ray_lw4[b]; T->chunk4[b] = t->chunk[b]; T->swap1[b] = t->swap1[b]; T->swap4[b] = t->swap4[b];
+    }
     return PCAS_OK;
 }
 
@@ -944,36 +959,45 @@ int pcas_autotune(const void* f0, const void* mean, const void* U, int dtype, in
         }
         return PCAS_OK;
     };
-    // 2. warp patch widths of the two projectors (each judged by its own kernel)
-    if (rc == PCAS_OK) {
-        double t1best = 0.0, t4best = 0.0;
-        int c1 = best.lw1, c4 = best.lw4;
+    // 2. per angle bin, the patch width and chunk of the four-candidate projector
+    for (int b = 0; b < NBIN && rc == PCAS_OK; b++) {
+        if (!ok_bin[b]) continue;
+        double bestt = 0.0;
+        int blw = best.lw4[b], bch = best.chunk4[b];
+        bool first = true;
         for (int lw = 2; lw <= 4 && rc == PCAS_OK; lw++) {
-            Tune X = best;
-            X.lw1 = X.lw4 = lw;
-            double t1 = 0.0, t4 = 0.0;
-            int used = 0;
-            for (int q = 0; q < 4 && rc == PCAS_OK; q++) {
-                if (!ok_bin[probe[q]]) continue;
-                rc = tr.run(X, probe[q], a);
-                t1 += a[PCAS_K_DRR_SOLVER];
-                t4 += a[PCAS_K_DRR_BATCH];
-                used++;
+            const int chunks[3] = {12, 16, 24};
+            for (int c = 0; c < 3 && rc == PCAS_OK; c++) {
+                Tune X = best;
+                X.lw4[b] = (unsigned char)lw;
+                X.chunk4[b] = (unsigned char)chunks[c];
+                rc = tr.run(X, b, a);
+                if (rc != PCAS_OK || a[PCAS_K_DRR_BATCH] <= 0.0) continue;
+                if (first || a[PCAS_K_DRR_BATCH] < bestt) {
+                    bestt = a[PCAS_K_DRR_BATCH];
+                    blw = lw;
+                    bch = chunks[c];
+                    first = false;
+                }
             }
-            if (rc != PCAS_OK || !used) continue;
-            if (lw == 2 || t1 < t1best) { t1best = t1; c1 = lw; }
-            if (lw == 2 || t4 < t4best) { t4best = t4; c4 = lw; }
         }
-        best.lw1 = c1;
-        best.lw4 = c4;
+        best.lw4[b] = (unsigned char)blw;
+        best.chunk4[b] = (unsigned char)bch;
     }
-    // 3. chunk of the four-candidate projector
+    // 3. patch width and chunk of the one-volume projector (0: it reads through L1)
     if (rc == PCAS_OK) {
-        const int ch[3] = {12, 16, 24};
-        const int k4[1] = {PCAS_K_DRR_BATCH};
-        int c = best.chunk;
-        rc = sweep([](Tune& X, int v) { X.chunk = v; }, ch, 3, k4, 1, probe, 4, &c);
-        best.chunk = c;
+        const int lws[3] = {2, 3, 4};
+        const int k1[1] = {PCAS_K_DRR_SOLVER};
+        int c = best.lw1;
+        rc = sweep([](Tune& X, int v) { X.lw1 = v; }, lws, 3, k1, 1, probe, 4, &c);
+        best.lw1 = c;
+    }
+    if (rc == PCAS_OK) {
+        const int ch1[3] = {0, 32, 64};
+        const int k1[1] = {PCAS_K_DRR_SOLVER};
+        int c = best.chunk1;
+        rc = sweep([](Tune& X, int v) { X.chunk1 = v; }, ch1, 3, k1, 1, probe, 4, &c);
+        best.chunk1 = c;
     }
     // 4. voxel tile and gather size of the gradient pass
     if (rc == PCAS_OK) {

@@ -26,6 +26,8 @@ struct View {
     float step;              // ray-march step, mm
     int swap1, swap4;        // layout of the one-volume / four-candidate solver volumes:
                              // 1 = x and y exchanged (see solver_pad), chosen per angle
+    int lw1, lw4;            // projector warp patches (ray_pixel), chosen per angle
+    int chunk1, chunk4;      // projector chunks (ray_sums_staged), chosen per angle
 };
 
 struct Grid {
@@ -171,7 +173,9 @@ __device__ __forceinline__ float tri_dense(const T* __restrict__ f, const Grid& 
     float zx = qx - fx, zy = qy - fy, zz = qz - fz;
     const int sy = g.nx, sz = g.nx * g.ny;    // 32-bit offsets: volumes have < 2^31 voxels
     float v000, v100, v010, v110, v001, v101, v011, v111;
-    if (lx >= 0 && ly >= 0 && lz >= 0 && lx < g.nx - 1 && ly < g.ny - 1 && lz < g.nz - 1) {
+    // interior cell (all eight taps in the grid): 0 <= l < n - 1 per axis, as one unsigned compare
+    if ((unsigned)lx < (unsigned)(g.nx - 1) && (unsigned)ly < (unsigned)(g.ny - 1) &&
+        (unsigned)lz < (unsigned)(g.nz - 1)) {
         const T* b = f + lz * sz + ly * sy + lx;
         v000 = ldg_f(b);           v100 = ldg_f(b + 1);
         v010 = ldg_f(b + sy);      v110 = ldg_f(b + sy + 1);
@@ -370,13 +374,16 @@ __device__ bool block_reduce_last(const float (&v)[NV], Reduce red, unsigned int
 // below, or the ones pcas_autotune measured fastest for the bucket.
 enum { NBIN = 8 };            // 22.5-degree bins of the gantry angle modulo 180 degrees
 struct Tune {
-    int lw1, lw4;             // log2 of a warp's patch width in pixels along u (2..4);
-                              // the patch is (1 << lw) x (32 >> lw), four warps per block
-                              // stacked along v; 1: one-volume, 4: four-candidate projector
-    int chunk;                // sample indices per staged chunk, four-candidate projector
+    int lw1;                  // log2 of a warp's patch width in pixels along u (2..4) of the
+                              // one-volume projector; the patch is (1 << lw) x (32 >> lw),
+                              // four warps per block stacked along v
+    int chunk1;               // sample indices per staged chunk of the one-volume projector;
+                              // 0: it marches through L1 (no staging)
     int vt;                   // voxel tile of the gradient pass (vox_tile)
-    int adj_mult;             // gather blocks = adj_mult x the resident blocks of 256 threads
-    unsigned char swap1[NBIN], swap4[NBIN];   // volume layouts per angle bin (solver_pad)
+    int adj_mult;             // gather blocks per SM
+    unsigned char lw4[NBIN];      // per angle bin: patch width of the four-candidate projector,
+    unsigned char chunk4[NBIN];   // its staged chunk,
+    unsigned char swap1[NBIN], swap4[NBIN];   // and the volume layouts (solver_pad)
 };
 
 // Voxel tiles of the gradient pass (256 voxels): log2 of the x, y, z extents.
@@ -406,7 +413,10 @@ inline long adj_tiles_max(int nx, int ny, int nz) {
 }
 
 // Blocks of the solver projector for a patch width of 1 << lw pixels
-// (blocks of 128 rays: (1 << lw) x (128 >> lw) pixels).
+// (blocks of 128 rays: (1 << lw) x (128 >> lw) pixels).  The solver launches
+// drr_blocks(nu, nv) blocks, enough for every width; with the width read from
+// the view, a block's index maps to (bx, by) = (blk % gx, blk / gx) and blocks
+// past the detector have no rays.
 inline unsigned drr_blocks_x(int nu, int lw) { return (unsigned)((nu + (1 << lw) - 1) >> lw); }
 inline unsigned drr_blocks_y(int nv, int lw) { return (unsigned)((nv + (128 >> lw) - 1) / (128 >> lw)); }
 inline unsigned drr_blocks(int nu, int nv) {           // the largest grid over lw = 2..4

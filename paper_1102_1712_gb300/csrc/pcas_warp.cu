@@ -175,20 +175,25 @@ k_warp_pca(const T* __restrict__ f0, const T* __restrict__ mean,
 // coefficient vectors; each DVF is formed in the same operation order as the
 // single-volume warp, so a candidate's volume is bit-identical to a lone
 // evaluation.  Output: one float4 (f_0..f_3) per voxel, zero-halo layout.
-template <typename T>
+template <typename T, int KT>
 __global__ void __launch_bounds__(kWarpThreads)
 k_warp_batch(const T* __restrict__ f0, const T* __restrict__ mean,
-             const T* __restrict__ U, int K, const SolveState* st, Grid g, const View* __restrict__ Vp,
+             const T* __restrict__ U, const SolveState* st, Grid g, const View* __restrict__ Vp,
              float4* __restrict__ fpad4, int* __restrict__ box_out) {
     if (st->phase >= PH_STOP || st->nvalid < 2) return;
     const int swp = Vp ? Vp->swap4 : 0;
     const Pad pd = solver_pad(g.nx, g.ny, g.nz, swp);
-    __shared__ float s_w[TRIAL_BATCH][PCAS_KMAX];
-    if (threadIdx.x < TRIAL_BATCH * PCAS_KMAX) {
-        const int j = threadIdx.x / PCAS_KMAX, k = threadIdx.x % PCAS_KMAX;
-        s_w[j][k] = k < K ? (float)st->wt[j][k] : 0.0f;
+    __shared__ float s_w[TRIAL_BATCH][KT];
+    if (threadIdx.x < TRIAL_BATCH * KT) {
+        const int j = threadIdx.x / KT, k = threadIdx.x % KT;
+        s_w[j][k] = (float)st->wt[j][k];
     }
     __syncthreads();
+    float wk[TRIAL_BATCH][KT];
+#pragma unroll
+    for (int b = 0; b < TRIAL_BATCH; b++)
+#pragma unroll
+        for (int kk = 0; kk < KT; kk++) wk[b][kk] = s_w[b][kk];
     int bx[6] = {BOX_EMPTY, BOX_EMPTY, BOX_EMPTY, BOX_EMPTY, BOX_EMPTY, BOX_EMPTY};
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
     const long N = (long)g.nx * g.ny * g.nz;
@@ -201,14 +206,18 @@ k_warp_batch(const T* __restrict__ f0, const T* __restrict__ mean,
 #pragma unroll
             for (int b = 0; b < TRIAL_BATCH; b++) x[b][c] = m;
         }
-        for (int kk = 0; kk < K; kk++) {
+        const T* u0 = U + n;
+        float u[KT][3];
 #pragma unroll
-            for (int c = 0; c < 3; c++) {
-                const float u = ldcs_f(U + ((long)kk * 3 + c) * N + n);
+        for (int kk = 0; kk < KT; kk++)
 #pragma unroll
-                for (int b = 0; b < TRIAL_BATCH; b++) x[b][c] = fmaf(s_w[b][kk], u, x[b][c]);
-            }
-        }
+            for (int c = 0; c < 3; c++) u[kk][c] = ldcs_f(u0 + (kk * 3 + c) * N);
+#pragma unroll
+        for (int kk = 0; kk < KT; kk++)      // Eq. (1) in the order of the single-volume warp
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+#pragma unroll
+                for (int b = 0; b < TRIAL_BATCH; b++) x[b][c] = fmaf(wk[b][kk], u[kk][c], x[b][c]);
         float o[TRIAL_BATCH];
 #pragma unroll
         for (int b = 0; b < TRIAL_BATCH; b++)
@@ -267,6 +276,20 @@ cudaError_t warp_pca_t(const void* f0, const void* mean, const void* U, int K, W
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t warp_batch_t(const T* f0, const T* mean, const T* U, int K, const SolveState* st, Grid g,
+                         const View* Vd, float4* fpad4, int* box, const RowLaunch& L, cudaStream_t s) {
+    switch (K) {
+#define PCAS_WB_CASE(KK) \
+        case KK: k_warp_batch<T, KK><<<L.grid, L.threads, 0, s>>>(f0, mean, U, st, g, Vd, fpad4, box); break;
+        PCAS_WB_CASE(1) PCAS_WB_CASE(2) PCAS_WB_CASE(3) PCAS_WB_CASE(4)
+        PCAS_WB_CASE(5) PCAS_WB_CASE(6) PCAS_WB_CASE(7) PCAS_WB_CASE(8)
+#undef PCAS_WB_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 #define PCAS_DT_DISPATCH(dt, CALL)                                         \
@@ -298,10 +321,8 @@ cudaError_t launch_warp_batch(const void* f0, const void* mean, const void* U, i
                               const SolveState* st, Grid g, const View* Vd, float4* fpad4, cudaStream_t s) {
     const RowLaunch L = row_launch(g, 1);
     int* box = const_cast<int*>(st->box[1]);
-    PCAS_DT_DISPATCH(dt, (k_warp_batch<T><<<L.grid, L.threads, 0, s>>>(
-                              static_cast<const T*>(f0), static_cast<const T*>(mean),
-                              static_cast<const T*>(U), K, st, g, Vd, fpad4, box),
-                          cudaGetLastError()))
+    PCAS_DT_DISPATCH(dt, (warp_batch_t<T>(static_cast<const T*>(f0), static_cast<const T*>(mean),
+                                          static_cast<const T*>(U), K, st, g, Vd, fpad4, box, L, s)))
 }
 
 #undef PCAS_DT_DISPATCH

@@ -509,29 +509,33 @@ class Batch:
 
 class Tuning(C.Structure):
     """pcas_tuning: launch shapes of one size bucket (include/pcasolve.h)."""
-    _fields_ = [("ray_lw1", C.c_int), ("ray_lw4", C.c_int), ("chunk", C.c_int), ("voxel_tile", C.c_int),
-                ("gather_per_sm", C.c_int), ("swap1", C.c_ubyte * 8), ("swap4", C.c_ubyte * 8)]
+    _fields_ = [("ray_lw1", C.c_int), ("chunk1", C.c_int), ("voxel_tile", C.c_int), ("gather_per_sm", C.c_int),
+                ("ray_lw4", C.c_ubyte * 8), ("chunk", C.c_ubyte * 8), ("swap1", C.c_ubyte * 8),
+                ("swap4", C.c_ubyte * 8)]
+    SCALARS = ("ray_lw1", "chunk1", "voxel_tile", "gather_per_sm")
+    PER_BIN = ("ray_lw4", "chunk", "swap1", "swap4")
 
     def as_dict(self):
-        return {"ray_lw1": self.ray_lw1, "ray_lw4": self.ray_lw4, "chunk": self.chunk,
-                "voxel_tile": self.voxel_tile, "gather_per_sm": self.gather_per_sm,
-                "swap1": list(self.swap1), "swap4": list(self.swap4)}
+        d = {k: getattr(self, k) for k in self.SCALARS}
+        d.update({k: list(getattr(self, k)) for k in self.PER_BIN})
+        return d
 
 
 def _tuning_struct(d):
     t = Tuning()
-    for k in ("ray_lw1", "ray_lw4", "chunk", "voxel_tile", "gather_per_sm"):
+    for k in Tuning.SCALARS:
         setattr(t, k, int(d[k]))
-    for k in ("swap1", "swap4"):
+    for k in Tuning.PER_BIN:
         arr = getattr(t, k)
-        for b, v in enumerate(d[k]):
+        vals = d[k] if hasattr(d[k], "__len__") else [d[k]] * 8
+        for b, v in enumerate(vals):
             arr[b] = int(v)
     return t
 
 
 def autotune(f0, mean, U, y, vol, cb, params, w_init=None, ws: Workspace = None, stream=None):
     """Measure launch shapes on this problem and store the fastest for its size
-    bucket (synchronous, about 60 short trial solves).  Returns the entry."""
+    bucket (synchronous, about 130 short trial solves).  Returns the entry."""
     K = _K(U, vol)
     N = _nvox(vol)
     dt = U.dtype

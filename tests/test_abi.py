@@ -160,15 +160,19 @@ def test_tuning_table_host_only(lib):
     cb = S.cone_beam(128, 96, 3.1, 3.1)
     P.tuning_clear()
     d = P.tuning_get(vol, cb, 3)
-    assert d["ray_lw1"] == 3 and d["chunk"] == 16 and d["swap4"] == [0, 0, 0, 1, 1, 1, 0, 0]
-    t = dict(ray_lw1=2, ray_lw4=4, chunk=24, voxel_tile=5, gather_per_sm=2, swap1=[1] * 8, swap4=[0] * 8)
+    assert d == dict(ray_lw1=3, chunk1=0, voxel_tile=0, gather_per_sm=8, ray_lw4=[3] * 8, chunk=[16] * 8,
+                     swap1=[0, 0, 0, 1, 1, 1, 0, 0], swap4=[0, 0, 0, 1, 1, 1, 0, 0])
+    t = dict(ray_lw1=2, chunk1=64, voxel_tile=5, gather_per_sm=2, ray_lw4=[2, 3, 4, 2, 3, 4, 2, 3],
+             chunk=[12, 16, 24, 2, 64, 12, 16, 24], swap1=[1] * 8, swap4=[0, 1] * 4)
     P.tuning_set(vol, cb, 3, t)
     assert P.tuning_get(vol, cb, 3) == t
     assert P.tuning_get(S.volume(60, 64, 32, 4.0, 4.0, 4.0), cb, 3) == t        # same bucket (x in 33..64)
     assert P.tuning_get(S.volume(96, 64, 32, 4.0, 4.0, 4.0), cb, 3) == d        # next bucket
     assert P.tuning_get(vol, cb, 5) == d and P.tuning_get(vol, cb, 3, dtype=P.BF16) == d
-    for bad in (dict(t, ray_lw1=5), dict(t, chunk=13), dict(t, chunk=66), dict(t, voxel_tile=6),
-                dict(t, gather_per_sm=0), dict(t, gather_per_sm=27), dict(t, swap1=[2] + [0] * 7)):
+    for bad in (dict(t, ray_lw1=5), dict(t, chunk1=-2), dict(t, chunk1=33), dict(t, chunk1=130),
+                dict(t, voxel_tile=6), dict(t, gather_per_sm=0), dict(t, gather_per_sm=27),
+                dict(t, ray_lw4=[1] + [3] * 7), dict(t, chunk=[13] + [16] * 7), dict(t, chunk=[0] * 8),
+                dict(t, chunk=[66] * 8), dict(t, swap1=[2] + [0] * 7)):
         with pytest.raises(P.PcasError):
             P.tuning_set(vol, cb, 3, bad)
     P.tuning_clear()
