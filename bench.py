@@ -202,22 +202,28 @@ def kernel_source_hash(kernel):
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary of this kernel on this
-    workload, or None when the kernel sources changed since that capture."""
+def ncu_field(kernel, field, cast=int):
+    """One field of the committed ncu summary of this kernel on the sequence
+    workload (``field: value`` lines), or None when the kernel sources changed
+    since that capture."""
     path = os.path.join(ROOT, "profiles", f"{KERNEL_FILE[kernel]}_sequence_256x256x100_K3_512x384.md")
     try:
         text = open(path).read()
     except OSError:
         return None
     fields = dict(line.split(":", 1) for line in text.splitlines()
-                  if line.startswith(("kernel_source_sha256_16:", "traffic_bytes_per_launch:")))
+                  if line.startswith(("kernel_source_sha256_16:", field + ":")))
     if fields.get("kernel_source_sha256_16", "").strip() != kernel_source_hash(kernel):
         return None
     try:
-        return int(fields["traffic_bytes_per_launch"])
+        return cast(fields[field].strip())
     except (KeyError, ValueError):
         return None
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)."""
+    return ncu_field(kernel, "traffic_bytes_per_launch")
 
 
 def peaks():
@@ -412,6 +418,7 @@ def run_ours(args, ws_, rank, local):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["achieved_gbs"],
                      "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": kernels[dom]["frac_hbm"],
                      "traffic": ncu_traffic(dom), "peak_source": pk_kind,
+                     "l1_pipe_frac": ncu_field(dom, "l1tex_throughput_frac", float),
                      "path_alg_gbs": round(total_alg / (ms_host / 1e3) / 1e9, 1),
                      "path_frac": round(total_alg / (ms_host / 1e3) / 1e9 / pk["hbm_gbs"], 4),
                      "note": "kernel durations from CUDA events in the host-driven pass over the same "

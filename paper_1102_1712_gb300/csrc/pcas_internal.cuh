@@ -472,7 +472,8 @@ cudaError_t launch_resid(const float* pbuf, const float* y, const View& Vh, cons
 cudaError_t launch_adjoint_plain(const float* img, Grid g, const View& V, float* gout,
                                  cudaStream_t s);
 // Scratch of the gradient pass: compacted voxels with a non-zero warp
-// Jacobian (index and h_k, per voxel tile of 256) and the tile counts / offsets.
+// Jacobian (place in the voxel tile and h_k, per tile of 256) and the tile
+// counts / offsets.
 struct AdjScratch {
     int* act_idx;       // ntiles * 256
     float* act_h;       // K * ntiles * 256
