@@ -178,9 +178,9 @@ def kernel_bytes(N, M, K, has_mean):
     model = 12 * K * N + (12 * N if has_mean else 0)
     return {
         "warp_pca": model + 4 * N + 4 * N,           # model read, f0 read once, f written
-        "warp_batch": model + 4 * N + 16 * N,        # model + f0 once, four candidate volumes written
+        "warp_batch": model + 4 * N + 20 * N,        # model + f0 once, five candidate volumes written
         "drr_solver": 4 * N + 4 * M + 4 * M,         # f read once, y read, p written
-        "drr_batch": 16 * N + 4 * M + 16 * M,        # four volumes read once, y read, four p written
+        "drr_batch": 20 * N + 4 * M + 20 * M,        # five volumes read once, y read, five p written
         "resid": 4 * M + 4 * M + 32 * M,             # p, y read; ray table written
         "adjoint_grad": model + 4 * N + 32 * M,      # model + f0 re-read; ray table read
     }
@@ -434,8 +434,8 @@ def run_ours(args, ws_, rank, local):
         "solver": {"iters_mean": round(float(iters.mean()), 3), "evals_mean": round(float(evals.mean()), 3)},
         "e2e": {"value": round(ws_ * K_ / te_s, 3), "unit": "projections/s",
                 "h2d_bytes_per_step": 4 * M,
-                # solver state read back once per solve (920 B), 32 B of centroid
-                "d2h_bytes_per_step": 952},
+                # solver state read back once per solve (1040 B), 32 B of centroid
+                "d2h_bytes_per_step": 1072},
     }
     if ws_ == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(vol, f0, c_ref, U, trace, train, angles, ys, W_)

@@ -173,7 +173,7 @@ int cost_grad_static(const float* f0, const float* mean, const float* U, int K, 
  * J(w + mu d) <= J(w) - alpha mu ||G||; if none passes, no step is taken and
  * the solve ends.  It also ends after max_iter iterations or at G = 0.
  * f0, mean, U, y, ws: device; w_init, w_out (K), params, stats: host.
- * The backtracking candidates are evaluated up to four at a time (one warp and
+ * The backtracking candidates are evaluated up to five at a time (one warp and
  * one projection pass for all of them) and tested in schedule order, so the
  * accepted step is the one the one-at-a-time rule would take; stats->evals
  * counts evaluations as that rule would.  Synchronous (one host read of a
@@ -285,10 +285,10 @@ int lp_predict(const double* hist, const double* c, int K, int L, double* w0);
  *   gather_per_sm     blocks of the gradient gather per SM (1..26)
  * and per 22.5-degree bin of the gantry angle modulo 180 degrees (bin b is
  * centred on 22.5 b degrees):
- *   ray_lw4[b]        patch width of the four-candidate projector (2..4)
+ *   ray_lw4[b]        patch width of the batch projector (2..4)
  *   chunk[b]          its sample indices per shared-memory chunk (even, 2..64)
- *   swap1[b], swap4[b]  layout of the one-volume / four-candidate solver
- *                     volumes: 0 = x fastest, 1 = y fastest
+ *   swap[b]           layout of the solver volumes: 0 = x fastest,
+ *                     1 = y fastest
  * Every call takes the entry of its bucket, or the defaults (3, 0, 0, 8; per
  * bin 3, 16, y fastest in bins 3..5) when there is none; a device-driven
  * solver takes the entry in force when it is created (the per-bin shapes
@@ -297,7 +297,7 @@ int lp_predict(const double* hist, const double* c, int K, int L, double* w0);
  * fixed table. */
 typedef struct {
     int ray_lw1, chunk1, voxel_tile, gather_per_sm;
-    unsigned char ray_lw4[8], chunk[8], swap1[8], swap4[8];
+    unsigned char ray_lw4[8], chunk[8], swap[8];
 } pcas_tuning;
 
 /* Measures shapes on this problem and stores the fastest in its bucket:
@@ -333,8 +333,8 @@ enum {
     PCAS_K_WARP_DVF = 7,     /* warp_volume                                     */
     PCAS_K_LOCALIZE = 8,     /* localize_tumor                                  */
     PCAS_K_INIT = 9,         /* solver state reset                              */
-    PCAS_K_WARP_BATCH = 10,  /* four line-search candidates warped at once      */
-    PCAS_K_DRR_BATCH = 11,   /* four candidates projected and tested at once    */
+    PCAS_K_WARP_BATCH = 10,  /* five line-search candidates warped at once      */
+    PCAS_K_DRR_BATCH = 11,   /* five candidates projected and tested at once    */
     PCAS_K_GRAD_F0 = 12,     /* dJ/df0: full backprojection + warp transpose    */
     PCAS_K_GRAPH = 13,       /* kernels run inside device-driven (graph) solves  */
     PCAS_K_SIDDON = 14,      /* drr_siddon                                      */

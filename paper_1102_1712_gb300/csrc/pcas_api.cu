@@ -175,7 +175,7 @@ int make_view(const pcas_vol* vol, const pcas_cb* cb, double step, View* V) {
     V->nu = cb->nu;
     V->nv = cb->nv;
     V->step = (float)step;
-    V->swap1 = V->swap4 = 0;                // launch shapes: set_layouts
+    V->swap = 0;                            // launch shapes: set_layouts
     V->lw1 = V->lw4 = 3;
     V->chunk1 = 0;
     V->chunk4 = 16;
@@ -206,7 +206,7 @@ Layout layout(const pcas_vol* vol, const pcas_cb* cb, int K) {
     L.state = off; off += align256(sizeof(SolveState));
     L.view = off; off += align256(sizeof(View));
     L.fpad = off; off += align256(npad * sizeof(float));                 // f(w), zero halo
-    L.fpad4 = off; off += align256(npad * sizeof(float4));               // four candidates
+    L.fpad4 = off; off += align256(npad * sizeof(float4));               // candidates 0-3 (4 in fpad)
     L.pbuf = off; off += align256((size_t)NBUF * M * sizeof(float));     // projection ring
     L.rayt = off; off += align256(2 * M * sizeof(float4));               // (step, r), (1/step, 0)
     L.part_drr = off; off += align256((size_t)drr_blocks(cb->nu, cb->nv) * DRR_PART_VALS * sizeof(double));
@@ -257,7 +257,7 @@ int bind_ws(void* ws, size_t ws_bytes, const pcas_vol* vol, const pcas_cb* cb, i
 }
 
 // ------------------------------------------------------------ launch shapes
-// Default shapes: 8 x 4 warp patches, 16-sample chunks for the four-candidate
+// Default shapes: 8 x 4 warp patches, 16-sample chunks for the batch
 // projector (the one-volume projector marches through L1), 8 x 8 x 4 voxel tiles,
 // eight gather blocks per SM, y-fastest solver volumes for angles near 90
 // (bins 67.5 ... 112.5 degrees).
@@ -270,7 +270,7 @@ Tune default_tune() {
     for (int b = 0; b < NBIN; b++) {
         T.lw4[b] = 3;
         T.chunk4[b] = 16;
-        T.swap1[b] = T.swap4[b] = (b >= 3 && b <= 5) ? 1 : 0;
+        T.swap[b] = (b >= 3 && b <= 5) ? 1 : 0;
     }
     return T;
 }
@@ -286,8 +286,7 @@ int angle_bin(double angle) {
 
 void set_layouts(View& V, const Tune& T, double angle) {
     const int b = angle_bin(angle);
-    V.swap1 = T.swap1[b];
-    V.swap4 = T.swap4[b];
+    V.swap = T.swap[b];
     V.lw1 = T.lw1;
     V.lw4 = T.lw4[b];
     V.chunk1 = T.chunk1;
@@ -499,7 +498,7 @@ int solve_host(const void* f0, const void* mean, const void* U, int dtype, int K
                     launch_adjoint_grad(W.rayt, g, W.view, f0, mean, U, dtype, K, 1, W.st, W.part_adj, W.adj, T.vt,
                                         adj_blocks, s));
         // Armijo backtracking over the schedule mu0, beta mu0, ...: the next (up
-        // to four) step sizes that the rule may still try are rendered and
+        // to five) step sizes that the rule may still try are rendered and
         // tested in one pass; the device accepts the first that passes, in
         // order.  The host mirrors the schedule only to size each batch, and
         // reads one flag per batch.
@@ -520,7 +519,7 @@ int solve_host(const void* f0, const void* mean, const void* U, int dtype, int K
                 break;
             }
             if (nvalid >= 2) {
-                PCAS_LAUNCH(PCAS_K_WARP_BATCH, s, launch_warp_batch(f0, mean, U, dtype, K, W.st, g, W.view, W.fpad4, s));
+                PCAS_LAUNCH(PCAS_K_WARP_BATCH, s, launch_warp_batch(f0, mean, U, dtype, K, W.st, g, W.view, W.fpad4, W.fpad, s));
                 PCAS_LAUNCH(PCAS_K_DRR_BATCH, s,
                             launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, TRIAL_BATCH,
                                               W.st, W.part_drr, T, s));
@@ -822,7 +821,7 @@ pcas_tuning to_public(const Tune& T) {
     pcas_tuning t;
     t.ray_lw1 = T.lw1; t.chunk1 = T.chunk1; t.voxel_tile = T.vt; t.gather_per_sm = T.adj_mult;
     for (int b = 0; b < NBIN; b++) {
-        t.ray_lw4[b] = T.lw4[b]; t.chunk[b] = T.chunk4[b]; t.swap1[b] = T.swap1[b]; t.swap4[b] = T.swap4[b];
+        t.ray_lw4[b] = T.lw4[b]; t.chunk[b] = T.chunk4[b]; t.swap[b] = T.swap[b];
     }
     return t;
 }
@@ -834,11 +833,11 @@ int from_public(const pcas_tuning* t, Tune* T) {
         return fail(PCAS_ERR_INVALID_ARG, "tuning field out of range");
     for (int b = 0; b < NBIN; b++)
         if (t->ray_lw4[b] < 2 || t->ray_lw4[b] > 4 || t->chunk[b] < 2 || t->chunk[b] > 64 || (t->chunk[b] & 1) ||
-            t->swap1[b] > 1 || t->swap4[b] > 1)
+            t->swap[b] > 1)
             return fail(PCAS_ERR_INVALID_ARG, "tuning field of angle bin %d out of range", b);
     T->lw1 = t->ray_lw1; T->chunk1 = t->chunk1; T->vt = t->voxel_tile; T->adj_mult = t->gather_per_sm;
     for (int b = 0; b < NBIN; b++) {
-        T->lw4[b] = t->ray_lw4[b]; T->chunk4[b] = t->chunk[b]; T->swap1[b] = t->swap1[b]; T->swap4[b] = t->swap4[b];
+        T->lw4[b] = t->ray_lw4[b]; T->chunk4[b] = t->chunk[b]; T->swap[b] = t->swap[b];
     }
     return PCAS_OK;
 }
@@ -918,23 +917,21 @@ int pcas_autotune(const void* f0, const void* mean, const void* U, int dtype, in
     double a[PCAS_K_COUNT];
     int rc = PCAS_OK;
     bool ok_bin[NBIN];
-    // 1. per angle bin, the layout of each solver volume: one-volume kernels
-    //    (warp + projector) and four-candidate kernels, timed together
+    // 1. per angle bin, the layout of the solver volumes, judged by every warp
+    //    and projector kernel together (they write and read the same buffers)
     for (int b = 0; b < NBIN && rc == PCAS_OK; b++) {
-        double t1[2] = {0, 0}, t4[2] = {0, 0};
+        double tt[2] = {0, 0};
         ok_bin[b] = true;
         for (int sw = 0; sw < 2 && ok_bin[b]; sw++) {
             Tune X = best;
-            X.swap1[b] = X.swap4[b] = (unsigned char)sw;
+            X.swap[b] = (unsigned char)sw;
             const int r = tr.run(X, b, a);
             if (r == PCAS_ERR_INVALID_ARG) { ok_bin[b] = false; break; }   // view invalid at this angle
             if (r != PCAS_OK) { rc = r; break; }
-            t1[sw] = a[PCAS_K_WARP_PCA] + a[PCAS_K_DRR_SOLVER];
-            t4[sw] = a[PCAS_K_WARP_BATCH] + a[PCAS_K_DRR_BATCH];
+            tt[sw] = a[PCAS_K_WARP_PCA] + a[PCAS_K_DRR_SOLVER] + 2.0 * (a[PCAS_K_WARP_BATCH] + a[PCAS_K_DRR_BATCH]);
         }
         if (rc != PCAS_OK || !ok_bin[b]) continue;
-        best.swap1[b] = t1[1] < t1[0] ? 1 : 0;
-        if (t4[0] > 0 && t4[1] > 0) best.swap4[b] = t4[1] < t4[0] ? 1 : 0;
+        best.swap[b] = tt[1] < tt[0] ? 1 : 0;
     }
     const int probe[4] = {0, 2, 4, 6};
     auto sweep = [&](auto apply, const int* cands, int ncand, const int* kinds, int nkinds, const int* bins,
@@ -959,7 +956,7 @@ int pcas_autotune(const void* f0, const void* mean, const void* U, int dtype, in
         }
         return PCAS_OK;
     };
-    // 2. per angle bin, the patch width and chunk of the four-candidate projector
+    // 2. per angle bin, the patch width and chunk of the batch projector
     for (int b = 0; b < NBIN && rc == PCAS_OK; b++) {
         if (!ok_bin[b]) continue;
         double bestt = 0.0;
@@ -1322,7 +1319,7 @@ struct pcas_solver_s {
     cudaGraphExec_t exec;
     View view0;           // geometry at creation (grid sizes)
     Tune tune;            // launch shapes of the size bucket at creation (captured)
-    int layout;           // swap1 | swap4 << 1 of the last staged view; -1: buffers all zero
+    int layout;           // swap of the last staged view; -1: buffers all zero
 };
 
 struct pcas_batch_s {
@@ -1379,9 +1376,9 @@ int capture_solve(pcas_solver s, cudaGraph_t graph, cudaStream_t cs, const float
     k_ctrl_iter_end<<<1, 1, 0, cs>>>(W.st, s->h_outer);
     PCAS_G(cudaGetLastError());
     PCAS_G(cudaStreamEndCapture(cs, &done));
-    // one candidate batch: the four-volume pair or the one-volume pair runs
+    // one candidate batch: the batch pair or the one-volume pair runs
     PCAS_G(cudaStreamBeginCaptureToGraph(cs, inner_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    PCAS_G(launch_warp_batch(s->f0, s->mean, s->U, s->dtype, s->K, W.st, g, W.view, W.fpad4, cs));
+    PCAS_G(launch_warp_batch(s->f0, s->mean, s->U, s->dtype, s->K, W.st, g, W.view, W.fpad4, W.fpad, cs));
     PCAS_G(launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, s->y, W.pbuf, TRIAL_BATCH, W.st, W.part_drr,
                              s->tune, cs));
     PCAS_G(launch_warp_pca(s->f0, s->mean, s->U, s->dtype, s->K, wtrial, g, W.view, W.fpad, W.st->box[0], cs));
@@ -1404,7 +1401,7 @@ int solver_stage(pcas_solver s, double angle_rad, double off_u, double off_v, co
     PCAS_TRY(make_view(&s->vol, &cb, s->prm.step_mm, &V));
     PCAS_TRY(check_finite(w_init, s->K, "w_init"));
     set_layouts(V, s->tune, angle_rad);
-    const int lay = V.swap1 | V.swap4 << 1;
+    const int lay = V.swap;
     if (s->layout >= 0 && s->layout != lay)   // the other layout's voxels lie on this one's halo
         PCAS_CUDA(cudaMemsetAsync(s->W.fpad, 0, s->W.fpad_bytes + s->W.fpad4_bytes, st));
     s->layout = lay;

@@ -24,8 +24,8 @@ struct View {
     float u0, du, v0, dv;    // detector coordinates of pixel centres, mm
     int nu, nv;
     float step;              // ray-march step, mm
-    int swap1, swap4;        // layout of the one-volume / four-candidate solver volumes:
-                             // 1 = x and y exchanged (see solver_pad), chosen per angle
+    int swap;                // layout of the solver volumes: 1 = x and y exchanged
+                             // (see solver_pad), chosen per angle
     int lw1, lw4;            // projector warp patches (ray_pixel), chosen per angle
     int chunk1, chunk4;      // projector chunks (ray_sums_staged), chosen per angle
 };
@@ -66,8 +66,11 @@ __host__ __device__ inline Pad solver_pad(int nx, int ny, int nz, int xy_swap) {
     return xy_swap ? make_pad(ny, nx, nz) : make_pad(nx, ny, nz);
 }
 
-// Trial step sizes evaluated together in one warp + projection pass.
-enum { TRIAL_BATCH = 4, NBUF = TRIAL_BATCH + 1 };
+// Trial step sizes evaluated together in one warp + projection pass: the
+// first four interleaved as float4 in the candidate buffer, the fifth in the
+// one-volume buffer (free during a batch).  Five covers the whole default
+// schedule mu0, beta mu0, ..., beta^4 mu0 >= mu_min of an iteration.
+enum { TRIAL_BATCH = 5, NBUF = TRIAL_BATCH + 1 };
 
 // ----------------------------------------------------------- solver state
 enum Phase : int {
@@ -95,7 +98,7 @@ struct SolveState {
     int max_iter, launches;               // launches: kernels run by a device-driven solve
     unsigned int counter[4];              // last-block counters (reset by the last block)
     // Bounding box of the non-zero voxels of the warped volume (slot 0: f,
-    // slot 1: the union of the four candidates), as {xmin, ymin, zmin, -xmax,
+    // slot 1: the union of the batch's candidates), as {xmin, ymin, zmin, -xmax,
     // -ymax, -zmax} so that both ends reduce with atomicMin; "empty" is
     // BOX_EMPTY everywhere.  Written by the warp kernels, read and reset by the
     // projector that consumes the volume.
@@ -381,9 +384,9 @@ struct Tune {
                               // 0: it marches through L1 (no staging)
     int vt;                   // voxel tile of the gradient pass (vox_tile)
     int adj_mult;             // gather blocks per SM
-    unsigned char lw4[NBIN];      // per angle bin: patch width of the four-candidate projector,
+    unsigned char lw4[NBIN];      // per angle bin: patch width of the batch projector,
     unsigned char chunk4[NBIN];   // its staged chunk,
-    unsigned char swap1[NBIN], swap4[NBIN];   // and the volume layouts (solver_pad)
+    unsigned char swap[NBIN];     // and the layout of the solver volumes (solver_pad)
 };
 
 // Voxel tiles of the gradient pass (256 voxels): log2 of the x, y, z extents.
@@ -443,13 +446,14 @@ cudaError_t launch_pca_dvf(const void* mean, const void* U, int dt, int K, const
                            float* dvf, cudaStream_t s);
 cudaError_t launch_warp_dvf(const void* f0, int dt, const float* dvf, Grid g, float* f, cudaStream_t s);
 // Solver warp: S = 1 writes f(w_src) to the scalar zero-halo buffer; S = 4
-// writes the four candidate volumes st->wt[0..3] interleaved (float4).
-// Vd (device, may be null): its swap1 (one volume) or swap4 (four candidates)
-// selects the layout (solver_pad); the bounding box is recorded in the same frame.
+// writes the batch: candidates st->wt[0..3] interleaved (float4) and wt[4] to fpad.
+// Vd (device, may be null): its swap selects the layout (solver_pad); the
+// bounding box is recorded in the same frame.
 cudaError_t launch_warp_pca(const void* f0, const void* mean, const void* U, int dt, int K, WSrc w,
                             Grid g, const View* Vd, float* fpad, int* box, cudaStream_t s);
 cudaError_t launch_warp_batch(const void* f0, const void* mean, const void* U, int dt, int K,
-                              const SolveState* st, Grid g, const View* Vd, float4* fpad4, cudaStream_t s);
+                              const SolveState* st, Grid g, const View* Vd, float4* fpad4, float* fpad,
+                              cudaStream_t s);
 cudaError_t launch_drr_plain(const float* f, Grid g, const View& V, float* p, cudaStream_t s);
 // Siddon geometry in double precision (world mm): source, unit axes, pixel
 // grid and the voxel grid (origin = centre of voxel (0,0,0)).
@@ -461,7 +465,7 @@ struct SidView {
 };
 cudaError_t launch_drr_siddon(const float* f, const SidView& V, float* p, cudaStream_t s);
 // Solver projector.  mode 0: first evaluation into buffer cur; mode 1: one
-// trial volume; mode 4: the four-volume batch (st->nvalid of them on the
+// trial volume; mode TRIAL_BATCH: the five-volume batch (st->nvalid of them on the
 // schedule).  Vh: the view on the host (grid size), Vd: the same in device
 // memory (read by the kernels, so captured launches stay view-independent).
 cudaError_t launch_drr_solver(const float* fpad, const float4* fpad4, Grid g,

@@ -108,7 +108,7 @@ k_warp_pca(const T* __restrict__ f0, const T* __restrict__ mean,
            float* __restrict__ fpad, int* __restrict__ box_out) {
     if (ws.phase && *ws.phase >= PH_STOP) return;
     if (ws.nvalid && *ws.nvalid != 1) return;
-    const int swp = Vp ? Vp->swap1 : 0;
+    const int swp = Vp ? Vp->swap : 0;
     const Pad pd = solver_pad(g.nx, g.ny, g.nz, swp);
     __shared__ float s_w[PCAS_KMAX];
     if (threadIdx.x < PCAS_KMAX) {
@@ -170,18 +170,19 @@ k_warp_pca(const T* __restrict__ f0, const T* __restrict__ mean,
     box_reduce(b, box_out);
 }
 
-// Four candidate volumes of the line search at once (Eq. 1 + A.5 for each
-// w + mu_j d): the motion model is read once per voxel and reused for the four
-// coefficient vectors; each DVF is formed in the same operation order as the
-// single-volume warp, so a candidate's volume is bit-identical to a lone
-// evaluation.  Output: one float4 (f_0..f_3) per voxel, zero-halo layout.
+// The five candidate volumes of a line-search batch at once (Eq. 1 + A.5 for
+// each w + mu_j d): the motion model is read once per voxel and reused for the
+// five coefficient vectors; each DVF is formed in the same operation order as
+// the single-volume warp, so a candidate's volume is bit-identical to a lone
+// evaluation.  Output: one float4 (f_0..f_3) per voxel in the candidate
+// buffer and f_4 in the one-volume buffer, zero-halo layout.
 template <typename T, int KT>
 __global__ void __launch_bounds__(kWarpThreads)
 k_warp_batch(const T* __restrict__ f0, const T* __restrict__ mean,
              const T* __restrict__ U, const SolveState* st, Grid g, const View* __restrict__ Vp,
-             float4* __restrict__ fpad4, int* __restrict__ box_out) {
+             float4* __restrict__ fpad4, float* __restrict__ fpad, int* __restrict__ box_out) {
     if (st->phase >= PH_STOP || st->nvalid < 2) return;
-    const int swp = Vp ? Vp->swap4 : 0;
+    const int swp = Vp ? Vp->swap : 0;
     const Pad pd = solver_pad(g.nx, g.ny, g.nz, swp);
     __shared__ float s_w[TRIAL_BATCH][KT];
     if (threadIdx.x < TRIAL_BATCH * KT) {
@@ -224,8 +225,10 @@ k_warp_batch(const T* __restrict__ f0, const T* __restrict__ mean,
             o[b] = tri_dense(f0, g, fmaf(x[b][0], g.inv_sx, (float)i), fmaf(x[b][1], g.inv_sy, (float)j),
                              fmaf(x[b][2], g.inv_sz, (float)k));
         const int a0 = swp ? j : i, a1 = swp ? i : j;
-        fpad4[pad_index(pd, a0, a1, k)] = make_float4(o[0], o[1], o[2], o[3]);
-        if (o[0] != 0.0f || o[1] != 0.0f || o[2] != 0.0f || o[3] != 0.0f) box_add(bx, a0, a1, k);
+        const long d = pad_index(pd, a0, a1, k);
+        fpad4[d] = make_float4(o[0], o[1], o[2], o[3]);
+        fpad[d] = o[4];
+        if (o[0] != 0.0f || o[1] != 0.0f || o[2] != 0.0f || o[3] != 0.0f || o[4] != 0.0f) box_add(bx, a0, a1, k);
     }
     box_reduce(bx, box_out);      // every thread of the block, one call site
 }
@@ -278,10 +281,11 @@ cudaError_t warp_pca_t(const void* f0, const void* mean, const void* U, int K, W
 
 template <typename T>
 cudaError_t warp_batch_t(const T* f0, const T* mean, const T* U, int K, const SolveState* st, Grid g,
-                         const View* Vd, float4* fpad4, int* box, const RowLaunch& L, cudaStream_t s) {
+                         const View* Vd, float4* fpad4, float* fpad, int* box, const RowLaunch& L,
+                         cudaStream_t s) {
     switch (K) {
 #define PCAS_WB_CASE(KK) \
-        case KK: k_warp_batch<T, KK><<<L.grid, L.threads, 0, s>>>(f0, mean, U, st, g, Vd, fpad4, box); break;
+        case KK: k_warp_batch<T, KK><<<L.grid, L.threads, 0, s>>>(f0, mean, U, st, g, Vd, fpad4, fpad, box); break;
         PCAS_WB_CASE(1) PCAS_WB_CASE(2) PCAS_WB_CASE(3) PCAS_WB_CASE(4)
         PCAS_WB_CASE(5) PCAS_WB_CASE(6) PCAS_WB_CASE(7) PCAS_WB_CASE(8)
 #undef PCAS_WB_CASE
@@ -318,11 +322,12 @@ cudaError_t launch_warp_pca(const void* f0, const void* mean, const void* U, int
 }
 
 cudaError_t launch_warp_batch(const void* f0, const void* mean, const void* U, int dt, int K,
-                              const SolveState* st, Grid g, const View* Vd, float4* fpad4, cudaStream_t s) {
+                              const SolveState* st, Grid g, const View* Vd, float4* fpad4, float* fpad,
+                              cudaStream_t s) {
     const RowLaunch L = row_launch(g, 1);
     int* box = const_cast<int*>(st->box[1]);
     PCAS_DT_DISPATCH(dt, (warp_batch_t<T>(static_cast<const T*>(f0), static_cast<const T*>(mean),
-                                          static_cast<const T*>(U), K, st, g, Vd, fpad4, box, L, s)))
+                                          static_cast<const T*>(U), K, st, g, Vd, fpad4, fpad, box, L, s)))
 }
 
 #undef PCAS_DT_DISPATCH

@@ -510,10 +510,9 @@ class Batch:
 class Tuning(C.Structure):
     """pcas_tuning: launch shapes of one size bucket (include/pcasolve.h)."""
     _fields_ = [("ray_lw1", C.c_int), ("chunk1", C.c_int), ("voxel_tile", C.c_int), ("gather_per_sm", C.c_int),
-                ("ray_lw4", C.c_ubyte * 8), ("chunk", C.c_ubyte * 8), ("swap1", C.c_ubyte * 8),
-                ("swap4", C.c_ubyte * 8)]
+                ("ray_lw4", C.c_ubyte * 8), ("chunk", C.c_ubyte * 8), ("swap", C.c_ubyte * 8)]
     SCALARS = ("ray_lw1", "chunk1", "voxel_tile", "gather_per_sm")
-    PER_BIN = ("ray_lw4", "chunk", "swap1", "swap4")
+    PER_BIN = ("ray_lw4", "chunk", "swap")
 
     def as_dict(self):
         d = {k: getattr(self, k) for k in self.SCALARS}

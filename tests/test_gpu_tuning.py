@@ -46,7 +46,7 @@ SHAPES = [dict(ray_lw1=2, chunk1=0, voxel_tile=1, gather_per_sm=4, ray_lw4=[4] *
 def test_every_shape_matches_the_oracle(P, prob, shape, swap):
     pb = prob
     d = to_dev(pb)
-    t = dict(shape, swap1=[swap] * 8, swap4=[1 - swap] * 8)
+    t = dict(shape, swap=[swap] * 8)
     P.tuning_set(pb["vol"], pb["cb"], 3, t)
     assert P.tuning_get(pb["vol"], pb["cb"], 3) == t
     w = np.array([0.4, -0.2, 0.1])
@@ -71,7 +71,7 @@ def test_autotune_stores_a_valid_entry(P, prob):
     P.tuning_clear()
     default = P.tuning_get(pb["vol"], pb["cb"], 3)
     assert default == dict(ray_lw1=3, chunk1=0, voxel_tile=0, gather_per_sm=8, ray_lw4=[3] * 8, chunk=[16] * 8,
-                           swap1=[0, 0, 0, 1, 1, 1, 0, 0], swap4=[0, 0, 0, 1, 1, 1, 0, 0])
+                           swap=[0, 0, 0, 1, 1, 1, 0, 0])
     prm = P.default_params(pb["step"])
     t = P.autotune(d["f0"], None, d["U"], d["y"], pb["vol"], pb["cb"], prm)
     print("autotuned:", t)
