@@ -128,3 +128,22 @@ def test_layout_follows_the_angle(P):
         assert abs(J - Jo) <= 1e-4 * Jo, (ang, J, Jo)
         assert np.linalg.norm(G - Go) <= 1e-3 * np.linalg.norm(Go), (ang, G, Go)
     sv.close()
+
+
+@pytest.mark.parametrize("mu_min,max_trials", [(0.04, 30), (0.0, 7), (0.0, 6), (0.0, 1), (0.011, 4)])
+def test_partial_batches_and_single_trials(P, mu_min, max_trials):
+    """Schedules that fill a batch of five only partly (mu_min cuts it to 3 or
+    4 steps, max_trials leaves 2 or 1) and the one-candidate pass: host loop and
+    device-driven graph agree bitwise, and both follow the oracle's one-at-a-time
+    rule."""
+    pb = tiny_problem()
+    d = to_dev(pb)
+    prm = P.default_params(pb["step"], mu_min=mu_min, max_iter=12, max_trials=max_trials)
+    w_h, st_h = P.solve_projection(d["f0"], None, d["U"], d["y"], pb["vol"], pb["cb"], np.zeros(3), prm)
+    sv = P.Solver(d["f0"], None, d["U"], pb["vol"], pb["cb"], prm)
+    w_g, st_g = sv.solve(d["y"], np.zeros(3))
+    sv.close()
+    assert np.array_equal(w_g, w_h) and st_g == st_h
+    wo, sto, _ = O.solve_projection(pb["f0"], None, pb["U"], pb["y"], pb["vol"], pb["cb"], np.zeros(3), prm)
+    assert st_h["iters"] == sto["iters"] and st_h["evals"] == sto["evals"], (st_h, sto)
+    assert np.linalg.norm(w_h - wo) < 2e-3, (w_h, wo)
