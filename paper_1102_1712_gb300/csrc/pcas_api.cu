@@ -460,11 +460,11 @@ int eval_gradient_pipeline(const void* f0, const void* mean, const void* U, int 
     ws.phase = &W.st->phase;
     PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, dt, K, ws, g, W.view, W.fpad, W.st->box[0], s));
     PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
-                launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, T, s));
+                launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, T, 0ull, 0, s));
     PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, W.view, 1, W.rayt, W.st, W.part_res, s));
     PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
                 launch_adjoint_grad(W.rayt, g, W.view, f0, mean, U, dt, K, step_setup, W.st, W.part_adj, W.adj,
-                                    T.vt, gather_blocks(T), s));
+                                    T.vt, gather_blocks(T), 0ull, 0, s));
     return PCAS_OK;
 }
 
@@ -482,21 +482,18 @@ int solve_host(const void* f0, const void* mean, const void* U, int dtype, int K
     PCAS_CUDA(cudaMemsetAsync(W.fpad, 0, W.fpad_bytes + W.fpad4_bytes, s));   // zero halos
     PCAS_TRY(launch_init(W.st, K, w_init, prm, s));
     PCAS_TRY(upload_view(W.view, V, s));
-    WSrc wcur{}, wtrial{};
+    WSrc wcur{};
     wcur.dev = W.st->w;
     wcur.phase = &W.st->phase;
-    wtrial.dev = W.st->wt[0];
-    wtrial.phase = &W.st->phase;
-    wtrial.nvalid = &W.st->nvalid;
     PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, dtype, K, wcur, g, W.view, W.fpad, W.st->box[0], s));
     PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
-                launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, T, s));
+                launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, T, 0ull, 0, s));
     int iters = 0, phase = PH_RUNNING;
     for (int it = 0; it < prm->max_iter; it++) {
         PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, W.view, it == 0, W.rayt, W.st, W.part_res, s));
         PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
                     launch_adjoint_grad(W.rayt, g, W.view, f0, mean, U, dtype, K, 1, W.st, W.part_adj, W.adj, T.vt,
-                                        adj_blocks, s));
+                                        adj_blocks, 0ull, 0, s));
         // Armijo backtracking over the schedule mu0, beta mu0, ...: the next (up
         // to five) step sizes that the rule may still try are rendered and
         // tested in one pass; the device accepts the first that passes, in
@@ -518,16 +515,10 @@ int solve_host(const void* f0, const void* mean, const void* U, int dtype, int K
                 if (phase == PH_RUNNING) phase = PH_STOP;
                 break;
             }
-            if (nvalid >= 2) {
-                PCAS_LAUNCH(PCAS_K_WARP_BATCH, s, launch_warp_batch(f0, mean, U, dtype, K, W.st, g, W.view, W.fpad4, W.fpad, s));
-                PCAS_LAUNCH(PCAS_K_DRR_BATCH, s,
-                            launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, TRIAL_BATCH,
-                                              W.st, W.part_drr, T, s));
-            } else {
-                PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, dtype, K, wtrial, g, W.view, W.fpad, W.st->box[0], s));
-                PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
-                            launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 1, W.st, W.part_drr, T, s));
-            }
+            PCAS_LAUNCH(PCAS_K_WARP_BATCH, s, launch_warp_batch(f0, mean, U, dtype, K, W.st, g, W.view, W.fpad4, W.fpad, s));
+            PCAS_LAUNCH(PCAS_K_DRR_BATCH, s,
+                        launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, TRIAL_BATCH, W.st, W.part_drr,
+                                          T, 0ull, 0, s));
             PCAS_CUDA(cudaMemcpyAsync(&phase, &W.st->phase, sizeof(int), cudaMemcpyDeviceToHost, s));
             PCAS_CUDA(cudaStreamSynchronize(s));
             if (phase != PH_RUNNING) break;
@@ -764,12 +755,12 @@ int cost_grad_f0(const float* f0, const float* mean, const float* U, int K, cons
     wsrc.phase = &W.st->phase;
     PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, DT_F32, K, wsrc, g, W.view, W.fpad, W.st->box[0], s));
     PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
-                launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, T, s));
+                launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, T, 0ull, 0, s));
     PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, W.view, 1, W.rayt, W.st, W.part_res, s));
     if (dJdw)
         PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
                     launch_adjoint_grad(W.rayt, g, W.view, f0, mean, U, DT_F32, K, 0, W.st, W.part_adj, W.adj,
-                                        T.vt, gather_blocks(T), s));
+                                        T.vt, gather_blocks(T), 0ull, 0, s));
     if (dJdf0)
         PCAS_LAUNCH(PCAS_K_GRAD_F0, s, launch_grad_f0(W.rayt, g, W.view, mean, U, K, W.st, z, zmax, acc, dJdf0, s));
     SolveState h;
@@ -1199,8 +1190,10 @@ int lp_predict(const double* hist, const double* c, int K, int L, double* w0) {
 // ===========================================================================
 // Device-driven solve: the loop of the Appendix as one CUDA graph.  Two nested
 // conditional WHILE nodes replace the host loop -- iterations, and candidate
-// batches inside an iteration -- and one-thread controller kernels set their
-// conditions from the solver state.  Both loops are bounded by construction:
+// batches inside an iteration.  The gradient's last block opens the batch
+// loop, the batch projector's last block decides each batch and whether
+// another follows, and a one-thread controller ends each iteration; every one
+// of these sets its condition on every path out.  Both loops are bounded by construction:
 // an iteration either accepts a step (at most max_iter of them) or ends the
 // solve, and every batch tries at least one step size of the iteration's
 // schedule (at most max_trials).  The view and the initial coefficients come
@@ -1239,27 +1232,14 @@ __global__ void k_init_dev(SolveState* st, const InitBlock* __restrict__ ib) {
 
 // After the first evaluation (init, warp, projection, this kernel).
 __global__ void k_ctrl_start(SolveState* st, cudaGraphConditionalHandle h_outer) {
-    st->launches += 3;
+    st->launches += 4;
     cudaGraphSetConditional(h_outer, (st->max_iter > 0 && st->phase < PH_STOP) ? 1u : 0u);
 }
 
-// Inside an iteration, after the gradient: run candidate batches while the line search is open.
-__global__ void k_ctrl_batches(SolveState* st, cudaGraphConditionalHandle h_inner) {
-    st->batches = 0;
-    cudaGraphSetConditional(h_inner, st->phase == PH_RUNNING ? 1u : 0u);
-}
-
-// End of a candidate batch (two warps, two projections -- one pair runs -- and this kernel).
-__global__ void k_ctrl_batch_end(SolveState* st, cudaGraphConditionalHandle h_inner) {
-    st->batches += 1;
-    st->launches += 5;
-    const bool more = st->phase == PH_RUNNING && st->batches <= st->max_trials;
-    cudaGraphSetConditional(h_inner, more ? 1u : 0u);
-}
-
-// End of an iteration (residual, three gradient kernels, batch start, this kernel).
+// End of an iteration (residual, three gradient kernels -- the last of which
+// opened the batch loop -- the batches, and this kernel).
 __global__ void k_ctrl_iter_end(SolveState* st, cudaGraphConditionalHandle h_outer) {
-    st->launches += 6;
+    st->launches += 5;
     int ph = st->phase;
     if (ph == PH_RUNNING) {          // batch cap reached without a decision: end the solve
         ph = PH_STOP;
@@ -1352,11 +1332,9 @@ int capture_solve(pcas_solver s, cudaGraph_t graph, cudaStream_t cs, const float
     WSrc wcur{};
     wcur.dev = W.st->w;
     wcur.phase = &W.st->phase;
-    WSrc wtrial = wcur;
-    wtrial.dev = W.st->wt[0];
-    wtrial.nvalid = &W.st->nvalid;
     PCAS_G(launch_warp_pca(s->f0, s->mean, s->U, s->dtype, s->K, wcur, g, W.view, W.fpad, W.st->box[0], cs));
-    PCAS_G(launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, s->y, W.pbuf, 0, W.st, W.part_drr, s->tune, cs));
+    PCAS_G(launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, s->y, W.pbuf, 0, W.st, W.part_drr, s->tune, 0ull, 0,
+                             cs));
     k_ctrl_start<<<1, 1, 0, cs>>>(W.st, s->h_outer);
     PCAS_G(cudaGetLastError());
     cudaGraph_t outer_body;
@@ -1368,23 +1346,18 @@ int capture_solve(pcas_solver s, cudaGraph_t graph, cudaStream_t cs, const float
     PCAS_G(cudaStreamBeginCaptureToGraph(cs, outer_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     PCAS_G(launch_resid(W.pbuf, s->y, V, W.view, -1, W.rayt, W.st, W.part_res, cs));
     PCAS_G(launch_adjoint_grad(W.rayt, g, W.view, s->f0, s->mean, s->U, s->dtype, s->K, 1, W.st, W.part_adj,
-                               W.adj, s->tune.vt, gather_blocks(s->tune), cs));
-    k_ctrl_batches<<<1, 1, 0, cs>>>(W.st, s->h_inner);
-    PCAS_G(cudaGetLastError());
+                               W.adj, s->tune.vt, gather_blocks(s->tune), s->h_inner, 1, cs));
     cudaGraph_t inner_body;
     PCAS_TRY(add_while(cs, s->h_inner, &inner_body));
     k_ctrl_iter_end<<<1, 1, 0, cs>>>(W.st, s->h_outer);
     PCAS_G(cudaGetLastError());
     PCAS_G(cudaStreamEndCapture(cs, &done));
-    // one candidate batch: the batch pair or the one-volume pair runs
+    // one candidate batch: warp and projection; the projection's last block
+    // decides the batch and whether another follows
     PCAS_G(cudaStreamBeginCaptureToGraph(cs, inner_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     PCAS_G(launch_warp_batch(s->f0, s->mean, s->U, s->dtype, s->K, W.st, g, W.view, W.fpad4, W.fpad, cs));
     PCAS_G(launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, s->y, W.pbuf, TRIAL_BATCH, W.st, W.part_drr,
-                             s->tune, cs));
-    PCAS_G(launch_warp_pca(s->f0, s->mean, s->U, s->dtype, s->K, wtrial, g, W.view, W.fpad, W.st->box[0], cs));
-    PCAS_G(launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, s->y, W.pbuf, 1, W.st, W.part_drr, s->tune, cs));
-    k_ctrl_batch_end<<<1, 1, 0, cs>>>(W.st, s->h_inner);
-    PCAS_G(cudaGetLastError());
+                             s->tune, s->h_inner, 1, cs));
     PCAS_G(cudaStreamEndCapture(cs, &done));
     return PCAS_OK;
 }

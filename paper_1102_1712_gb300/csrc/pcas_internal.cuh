@@ -436,7 +436,6 @@ struct WSrc {                 // where a PCA-model kernel takes w from
     float w[PCAS_KMAX];       // used when dev is null
     const double* dev;        // device w (solver state), K doubles
     const int* phase;         // early exit when *phase >= PH_STOP (may be null)
-    const int* nvalid;        // if set: run only for a one-candidate batch (*nvalid == 1)
 };
 
 // Storage type of f0 / mean / U (values of pcas_dtype in pcasolve.h).
@@ -445,8 +444,9 @@ enum DType : int { DT_F32 = 0, DT_BF16 = 1, DT_F16 = 2 };
 cudaError_t launch_pca_dvf(const void* mean, const void* U, int dt, int K, const float* w, Grid g,
                            float* dvf, cudaStream_t s);
 cudaError_t launch_warp_dvf(const void* f0, int dt, const float* dvf, Grid g, float* f, cudaStream_t s);
-// Solver warp: S = 1 writes f(w_src) to the scalar zero-halo buffer; S = 4
-// writes the batch: candidates st->wt[0..3] interleaved (float4) and wt[4] to fpad.
+// Solver warps: launch_warp_pca writes f(w_src) to the scalar zero-halo
+// buffer; launch_warp_batch writes the batch: candidates st->wt[0..3]
+// interleaved (float4) and wt[4] to fpad.
 // Vd (device, may be null): its swap selects the layout (solver_pad); the
 // bounding box is recorded in the same frame.
 cudaError_t launch_warp_pca(const void* f0, const void* mean, const void* U, int dt, int K, WSrc w,
@@ -464,13 +464,16 @@ struct SidView {
     int n[3], nu, nv;
 };
 cudaError_t launch_drr_siddon(const float* f, const SidView& V, float* p, cudaStream_t s);
-// Solver projector.  mode 0: first evaluation into buffer cur; mode 1: one
-// trial volume; mode TRIAL_BATCH: the five-volume batch (st->nvalid of them on the
+// Solver projector.  mode 0: first evaluation into buffer cur;
+// mode TRIAL_BATCH: the five-volume batch (st->nvalid of them on the
 // schedule).  Vh: the view on the host (grid size), Vd: the same in device
 // memory (read by the kernels, so captured launches stay view-independent).
+// hbatch / use_h: inside a device-driven solve the batch projector sets this
+// conditional handle to whether another candidate batch follows.
 cudaError_t launch_drr_solver(const float* fpad, const float4* fpad4, Grid g,
                               const View& Vh, const View* Vd, const float* y, float* pbuf, int mode,
-                              SolveState* st, double* part, const Tune& T, cudaStream_t s);
+                              SolveState* st, double* part, const Tune& T, unsigned long long hbatch,
+                              int use_h, cudaStream_t s);
 cudaError_t launch_resid(const float* pbuf, const float* y, const View& Vh, const View* Vd, int first,
                          float4* rayt, SolveState* st, double* part, cudaStream_t s);
 cudaError_t launch_adjoint_plain(const float* img, Grid g, const View& V, float* gout,
@@ -484,10 +487,12 @@ struct AdjScratch {
     int* tile_count;    // ntiles
     int* tile_off;      // ntiles + 1
 };
+// hbatch / use_h: inside a device-driven solve the gradient's last block opens
+// (or not) the iteration's candidate-batch loop by setting this handle.
 cudaError_t launch_adjoint_grad(const float4* rayt, Grid g, const View* V, const void* f0,
                                 const void* mean, const void* U, int dt, int K, int step_setup,
                                 SolveState* st, double* part, const AdjScratch& as, int vt, int max_blocks,
-                                cudaStream_t s);
+                                unsigned long long hbatch, int use_h, cudaStream_t s);
 // dJ/df0 = W^T (2 P^T r): z (N floats) and acc (N 64-bit) are scratch,
 // zmax_bits one word; out (N floats) receives the gradient.
 cudaError_t launch_grad_f0(const float4* rayt, Grid g, const View* V, const float* mean, const float* U,

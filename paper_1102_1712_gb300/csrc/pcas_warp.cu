@@ -107,7 +107,6 @@ k_warp_pca(const T* __restrict__ f0, const T* __restrict__ mean,
            const T* __restrict__ U, int K, WSrc ws, Grid g, const View* __restrict__ Vp,
            float* __restrict__ fpad, int* __restrict__ box_out) {
     if (ws.phase && *ws.phase >= PH_STOP) return;
-    if (ws.nvalid && *ws.nvalid != 1) return;
     const int swp = Vp ? Vp->swap : 0;
     const Pad pd = solver_pad(g.nx, g.ny, g.nz, swp);
     __shared__ float s_w[PCAS_KMAX];
@@ -181,7 +180,7 @@ __global__ void __launch_bounds__(kWarpThreads)
 k_warp_batch(const T* __restrict__ f0, const T* __restrict__ mean,
              const T* __restrict__ U, const SolveState* st, Grid g, const View* __restrict__ Vp,
              float4* __restrict__ fpad4, float* __restrict__ fpad, int* __restrict__ box_out) {
-    if (st->phase >= PH_STOP || st->nvalid < 2) return;
+    if (st->phase >= PH_STOP || st->nvalid < 1) return;    // same gate as the batch projector
     const int swp = Vp ? Vp->swap : 0;
     const Pad pd = solver_pad(g.nx, g.ny, g.nz, swp);
     __shared__ float s_w[TRIAL_BATCH][KT];
