@@ -191,7 +191,7 @@ int check_model(const void* mean, const void* U, int K) {
 
 // ------------------------------------------------------------- workspace
 struct Layout {
-    size_t state, view, fpad, fpad4, pbuf, rayt, part_drr, part_res, part_adj, act_idx, act_h, tile_count,
+    size_t state, view, f0h, fpad, fpad4, pbuf, rayt, part_drr, part_res, part_adj, act_idx, act_h, tile_count,
         tile_off, total;
 };
 
@@ -205,6 +205,7 @@ Layout layout(const pcas_vol* vol, const pcas_cb* cb, int K) {
     size_t off = 0;
     L.state = off; off += align256(sizeof(SolveState));
     L.view = off; off += align256(sizeof(View));
+    L.f0h = off; off += align256((size_t)f0h_count(vol->nx, vol->ny, vol->nz) * sizeof(float));  // f0, halo 3
     L.fpad = off; off += align256(npad * sizeof(float));                 // f(w), zero halo
     L.fpad4 = off; off += align256(npad * sizeof(float4));               // candidates 0-3 (4 in fpad)
     L.pbuf = off; off += align256((size_t)NBUF * M * sizeof(float));     // projection ring
@@ -224,6 +225,8 @@ Layout layout(const pcas_vol* vol, const pcas_cb* cb, int K) {
 struct Ws {
     SolveState* st;
     View* view;
+    float* f0h;
+    size_t f0h_bytes;
     float *fpad, *pbuf;
     float4 *fpad4, *rayt;
     double *part_drr, *part_res, *part_adj;
@@ -240,6 +243,8 @@ int bind_ws(void* ws, size_t ws_bytes, const pcas_vol* vol, const pcas_cb* cb, i
     char* b = static_cast<char*>(ws);
     W->st = reinterpret_cast<SolveState*>(b + L.state);
     W->view = reinterpret_cast<View*>(b + L.view);
+    W->f0h = reinterpret_cast<float*>(b + L.f0h);
+    W->f0h_bytes = L.fpad - L.f0h;
     W->fpad = reinterpret_cast<float*>(b + L.fpad);
     W->fpad4 = reinterpret_cast<float4*>(b + L.fpad4);
     W->pbuf = reinterpret_cast<float*>(b + L.pbuf);
@@ -450,6 +455,13 @@ int check_finite(const double* v, int n, const char* name) {
         if (rc_ != PCAS_OK) return rc_; \
     } while (0)
 
+// The halo copy of the reference CT for this call (zeroed, then filled).
+int stage_f0h(const void* f0, int dt, const Grid& g, const Ws& W, cudaStream_t s) {
+    PCAS_CUDA(cudaMemsetAsync(W.f0h, 0, W.f0h_bytes, s));
+    PCAS_LAUNCH(PCAS_K_INIT, s, launch_fill_f0h(f0, dt, g, W.f0h, s));
+    return PCAS_OK;
+}
+
 // Everything up to and including the gradient at st->w: warp, DRR with
 // moments, (A.1) + residual + J, fused adjoint gradient.
 int eval_gradient_pipeline(const void* f0, const void* mean, const void* U, int dt, int K, const float* y,
@@ -458,12 +470,13 @@ int eval_gradient_pipeline(const void* f0, const void* mean, const void* U, int 
     WSrc ws{};
     ws.dev = W.st->w;
     ws.phase = &W.st->phase;
-    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, dt, K, ws, g, W.view, W.fpad, W.st->box[0], s));
+    PCAS_TRY(stage_f0h(f0, dt, g, W, s));
+    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(W.f0h, mean, U, dt, K, ws, g, W.view, W.fpad, W.st->box[0], s));
     PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
                 launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, T, 0ull, 0, s));
     PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, W.view, 1, W.rayt, W.st, W.part_res, s));
     PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
-                launch_adjoint_grad(W.rayt, g, W.view, f0, mean, U, dt, K, step_setup, W.st, W.part_adj, W.adj,
+                launch_adjoint_grad(W.rayt, g, W.view, W.f0h, mean, U, dt, K, step_setup, W.st, W.part_adj, W.adj,
                                     T.vt, gather_blocks(T), 0ull, 0, s));
     return PCAS_OK;
 }
@@ -485,14 +498,15 @@ int solve_host(const void* f0, const void* mean, const void* U, int dtype, int K
     WSrc wcur{};
     wcur.dev = W.st->w;
     wcur.phase = &W.st->phase;
-    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, dtype, K, wcur, g, W.view, W.fpad, W.st->box[0], s));
+    PCAS_TRY(stage_f0h(f0, dtype, g, W, s));
+    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(W.f0h, mean, U, dtype, K, wcur, g, W.view, W.fpad, W.st->box[0], s));
     PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
                 launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, T, 0ull, 0, s));
     int iters = 0, phase = PH_RUNNING;
     for (int it = 0; it < prm->max_iter; it++) {
         PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, W.view, it == 0, W.rayt, W.st, W.part_res, s));
         PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
-                    launch_adjoint_grad(W.rayt, g, W.view, f0, mean, U, dtype, K, 1, W.st, W.part_adj, W.adj, T.vt,
+                    launch_adjoint_grad(W.rayt, g, W.view, W.f0h, mean, U, dtype, K, 1, W.st, W.part_adj, W.adj, T.vt,
                                         adj_blocks, 0ull, 0, s));
         // Armijo backtracking over the schedule mu0, beta mu0, ...: the next (up
         // to five) step sizes that the rule may still try are rendered and
@@ -515,7 +529,7 @@ int solve_host(const void* f0, const void* mean, const void* U, int dtype, int K
                 if (phase == PH_RUNNING) phase = PH_STOP;
                 break;
             }
-            PCAS_LAUNCH(PCAS_K_WARP_BATCH, s, launch_warp_batch(f0, mean, U, dtype, K, W.st, g, W.view, W.fpad4, W.fpad, s));
+            PCAS_LAUNCH(PCAS_K_WARP_BATCH, s, launch_warp_batch(W.f0h, mean, U, dtype, K, W.st, g, W.view, W.fpad4, W.fpad, s));
             PCAS_LAUNCH(PCAS_K_DRR_BATCH, s,
                         launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, TRIAL_BATCH, W.st, W.part_drr,
                                           T, 0ull, 0, s));
@@ -753,13 +767,14 @@ int cost_grad_f0(const float* f0, const float* mean, const float* U, int K, cons
     WSrc wsrc{};
     wsrc.dev = W.st->w;
     wsrc.phase = &W.st->phase;
-    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(f0, mean, U, DT_F32, K, wsrc, g, W.view, W.fpad, W.st->box[0], s));
+    PCAS_TRY(stage_f0h(f0, DT_F32, g, W, s));
+    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(W.f0h, mean, U, DT_F32, K, wsrc, g, W.view, W.fpad, W.st->box[0], s));
     PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
                 launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, T, 0ull, 0, s));
     PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, W.view, 1, W.rayt, W.st, W.part_res, s));
     if (dJdw)
         PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
-                    launch_adjoint_grad(W.rayt, g, W.view, f0, mean, U, DT_F32, K, 0, W.st, W.part_adj, W.adj,
+                    launch_adjoint_grad(W.rayt, g, W.view, W.f0h, mean, U, DT_F32, K, 0, W.st, W.part_adj, W.adj,
                                         T.vt, gather_blocks(T), 0ull, 0, s));
     if (dJdf0)
         PCAS_LAUNCH(PCAS_K_GRAD_F0, s, launch_grad_f0(W.rayt, g, W.view, mean, U, K, W.st, z, zmax, acc, dJdf0, s));
@@ -1230,9 +1245,9 @@ __global__ void k_init_dev(SolveState* st, const InitBlock* __restrict__ ib) {
         for (int j = 0; j < 6; j++) st->box[i][j] = BOX_EMPTY;
 }
 
-// After the first evaluation (init, warp, projection, this kernel).
+// After the first evaluation (init, copy of f0, warp, projection, this kernel).
 __global__ void k_ctrl_start(SolveState* st, cudaGraphConditionalHandle h_outer) {
-    st->launches += 4;
+    st->launches += 5;
     cudaGraphSetConditional(h_outer, (st->max_iter > 0 && st->phase < PH_STOP) ? 1u : 0u);
 }
 
@@ -1329,10 +1344,11 @@ int capture_solve(pcas_solver s, cudaGraph_t graph, cudaStream_t cs, const float
     PCAS_G(cudaMemcpyAsync(s->d_init, s->h_init, sizeof(InitBlock), cudaMemcpyHostToDevice, cs));
     k_init_dev<<<1, 32, 0, cs>>>(W.st, s->d_init);
     PCAS_G(cudaGetLastError());
+    PCAS_G(launch_fill_f0h(s->f0, s->dtype, g, W.f0h, cs));     // f0 may change between solves
     WSrc wcur{};
     wcur.dev = W.st->w;
     wcur.phase = &W.st->phase;
-    PCAS_G(launch_warp_pca(s->f0, s->mean, s->U, s->dtype, s->K, wcur, g, W.view, W.fpad, W.st->box[0], cs));
+    PCAS_G(launch_warp_pca(W.f0h, s->mean, s->U, s->dtype, s->K, wcur, g, W.view, W.fpad, W.st->box[0], cs));
     PCAS_G(launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, s->y, W.pbuf, 0, W.st, W.part_drr, s->tune, 0ull, 0,
                              cs));
     k_ctrl_start<<<1, 1, 0, cs>>>(W.st, s->h_outer);
@@ -1345,7 +1361,7 @@ int capture_solve(pcas_solver s, cudaGraph_t graph, cudaStream_t cs, const float
     PCAS_G(cudaGraphConditionalHandleCreate(&s->h_inner, outer_body, 0, cudaGraphCondAssignDefault));
     PCAS_G(cudaStreamBeginCaptureToGraph(cs, outer_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     PCAS_G(launch_resid(W.pbuf, s->y, V, W.view, -1, W.rayt, W.st, W.part_res, cs));
-    PCAS_G(launch_adjoint_grad(W.rayt, g, W.view, s->f0, s->mean, s->U, s->dtype, s->K, 1, W.st, W.part_adj,
+    PCAS_G(launch_adjoint_grad(W.rayt, g, W.view, W.f0h, s->mean, s->U, s->dtype, s->K, 1, W.st, W.part_adj,
                                W.adj, s->tune.vt, gather_blocks(s->tune), s->h_inner, 1, cs));
     cudaGraph_t inner_body;
     PCAS_TRY(add_while(cs, s->h_inner, &inner_body));
@@ -1355,7 +1371,7 @@ int capture_solve(pcas_solver s, cudaGraph_t graph, cudaStream_t cs, const float
     // one candidate batch: warp and projection; the projection's last block
     // decides the batch and whether another follows
     PCAS_G(cudaStreamBeginCaptureToGraph(cs, inner_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    PCAS_G(launch_warp_batch(s->f0, s->mean, s->U, s->dtype, s->K, W.st, g, W.view, W.fpad4, W.fpad, cs));
+    PCAS_G(launch_warp_batch(W.f0h, s->mean, s->U, s->dtype, s->K, W.st, g, W.view, W.fpad4, W.fpad, cs));
     PCAS_G(launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, s->y, W.pbuf, TRIAL_BATCH, W.st, W.part_drr,
                              s->tune, s->h_inner, 1, cs));
     PCAS_G(cudaStreamEndCapture(cs, &done));
@@ -1461,6 +1477,7 @@ int pcas_solver_create(pcas_solver* out, const void* f0, const void* mean, const
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&s->h_state, sizeof(SolveState), cudaHostAllocDefault);
     // zero the halos once: the warp kernels never write them
     if (e == cudaSuccess) e = cudaMemsetAsync(s->W.fpad, 0, s->W.fpad_bytes + s->W.fpad4_bytes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->W.f0h, 0, s->W.f0h_bytes, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaGraphCreate(&s->graph, 0);

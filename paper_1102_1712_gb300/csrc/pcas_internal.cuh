@@ -206,6 +206,44 @@ __device__ __forceinline__ float tri_dense(const T* __restrict__ f, const Grid& 
     return fmaf(zz, c1 - c0, c0);
 }
 
+// The reference CT as the solver kernels read it: float, with a zero halo
+// three voxels deep (voxel (i,j,k) at ((k+3)(ny+6) + (j+3))(nx+6) + (i+3)).
+// With positions clamped to [-2, n+1] as tri_dense does, all eight taps are
+// in the allocation and are exactly the zero-padded values tri_dense reads:
+// the same interpolant, bit for bit, without per-tap tests.
+enum { F0_HALO = 3 };
+__host__ __device__ inline long f0h_count(int nx, int ny, int nz) {
+    return (long)(nx + 2 * F0_HALO) * (ny + 2 * F0_HALO) * (nz + 2 * F0_HALO);
+}
+
+// The eight taps of the cell holding q (tap t = dx + 2 dy + 4 dz) and the
+// fractions, from the halo copy.
+__device__ __forceinline__ void taps_halo(const float* __restrict__ f, const Grid& g, float qx, float qy,
+                                          float qz, float v[8], float& zx, float& zy, float& zz) {
+    qx = fminf(fmaxf(qx, -2.0f), (float)g.nx + 1.0f);
+    qy = fminf(fmaxf(qy, -2.0f), (float)g.ny + 1.0f);
+    qz = fminf(fmaxf(qz, -2.0f), (float)g.nz + 1.0f);
+    const float fx = floorf(qx), fy = floorf(qy), fz = floorf(qz);
+    zx = qx - fx; zy = qy - fy; zz = qz - fz;
+    const int sy = g.nx + 2 * F0_HALO, sz = sy * (g.ny + 2 * F0_HALO);
+    const float* b = f + (((int)fz + F0_HALO) * sz + ((int)fy + F0_HALO) * sy + ((int)fx + F0_HALO));
+    v[0] = __ldg(b);           v[1] = __ldg(b + 1);
+    v[2] = __ldg(b + sy);      v[3] = __ldg(b + sy + 1);
+    v[4] = __ldg(b + sz);      v[5] = __ldg(b + sz + 1);
+    v[6] = __ldg(b + sz + sy); v[7] = __ldg(b + sz + sy + 1);
+}
+
+// Eq. (A.5) from the halo copy: tri_dense's result without its branches.
+__device__ __forceinline__ float tri_halo(const float* __restrict__ f, const Grid& g, float qx, float qy,
+                                          float qz) {
+    float v[8], zx, zy, zz;
+    taps_halo(f, g, qx, qy, qz, v, zx, zy, zz);
+    const float c00 = fmaf(zx, v[1] - v[0], v[0]), c10 = fmaf(zx, v[3] - v[2], v[2]);
+    const float c01 = fmaf(zx, v[5] - v[4], v[4]), c11 = fmaf(zx, v[7] - v[6], v[6]);
+    const float c0 = fmaf(zy, c10 - c00, c00), c1 = fmaf(zy, c11 - c01, c01);
+    return fmaf(zz, c1 - c0, c0);
+}
+
 // Same interpolant on the zero-halo layout: no bounds tests and no clamps.
 // Valid for q within half a voxel of [-1, n] (the caller guarantees it): the
 // floor is then in [-2, n] and every tap is a voxel or a halo zero.
@@ -444,14 +482,18 @@ enum DType : int { DT_F32 = 0, DT_BF16 = 1, DT_F16 = 2 };
 cudaError_t launch_pca_dvf(const void* mean, const void* U, int dt, int K, const float* w, Grid g,
                            float* dvf, cudaStream_t s);
 cudaError_t launch_warp_dvf(const void* f0, int dt, const float* dvf, Grid g, float* f, cudaStream_t s);
+// Copies f0 (storage type dt) into the interior of the halo copy f0h (whose
+// halo the caller has zeroed; it is never written).
+cudaError_t launch_fill_f0h(const void* f0, int dt, Grid g, float* f0h, cudaStream_t s);
 // Solver warps: launch_warp_pca writes f(w_src) to the scalar zero-halo
 // buffer; launch_warp_batch writes the batch: candidates st->wt[0..3]
 // interleaved (float4) and wt[4] to fpad.
 // Vd (device, may be null): its swap selects the layout (solver_pad); the
 // bounding box is recorded in the same frame.
-cudaError_t launch_warp_pca(const void* f0, const void* mean, const void* U, int dt, int K, WSrc w,
+// f0h: the halo copy of the reference CT (float); mean and U in storage type dt.
+cudaError_t launch_warp_pca(const float* f0h, const void* mean, const void* U, int dt, int K, WSrc w,
                             Grid g, const View* Vd, float* fpad, int* box, cudaStream_t s);
-cudaError_t launch_warp_batch(const void* f0, const void* mean, const void* U, int dt, int K,
+cudaError_t launch_warp_batch(const float* f0h, const void* mean, const void* U, int dt, int K,
                               const SolveState* st, Grid g, const View* Vd, float4* fpad4, float* fpad,
                               cudaStream_t s);
 cudaError_t launch_drr_plain(const float* f, Grid g, const View& V, float* p, cudaStream_t s);
@@ -489,7 +531,7 @@ struct AdjScratch {
 };
 // hbatch / use_h: inside a device-driven solve the gradient's last block opens
 // (or not) the iteration's candidate-batch loop by setting this handle.
-cudaError_t launch_adjoint_grad(const float4* rayt, Grid g, const View* V, const void* f0,
+cudaError_t launch_adjoint_grad(const float4* rayt, Grid g, const View* V, const float* f0h,
                                 const void* mean, const void* U, int dt, int K, int step_setup,
                                 SolveState* st, double* part, const AdjScratch& as, int vt, int max_blocks,
                                 unsigned long long hbatch, int use_h, cudaStream_t s);

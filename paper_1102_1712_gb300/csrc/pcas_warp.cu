@@ -99,11 +99,21 @@ k_warp_dvf(const T* __restrict__ f0, const float* __restrict__ dvf, Grid g, long
 // i = (blockIdx.x blockDim.x + threadIdx.x) V with V voxels per thread (no
 // index divisions; 32-bit voxel offsets, volumes have < 2^31 voxels).
 
+// The halo copy of the reference CT (see tri_halo): interior only.
+template <typename T>
+__global__ void __launch_bounds__(kWarpThreads)
+k_fill_f0h(const T* __restrict__ f0, Grid g, float* __restrict__ f0h) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= g.nx) return;
+    const long sy = g.nx + 2 * F0_HALO, sz = sy * (g.ny + 2 * F0_HALO);
+    f0h[(k + F0_HALO) * sz + (j + F0_HALO) * sy + (i + F0_HALO)] = ldg_f(f0 + ((long)k * g.ny + j) * g.nx + i);
+}
+
 // Fused DVF synthesis + warp into the zero-halo layout used by the solver.
 // VEC: 4 voxels per thread along x (nx % 4 == 0, 16-byte aligned model).
 template <bool VEC, typename T>
 __global__ void __launch_bounds__(kWarpThreads)
-k_warp_pca(const T* __restrict__ f0, const T* __restrict__ mean,
+k_warp_pca(const float* __restrict__ f0h, const T* __restrict__ mean,
            const T* __restrict__ U, int K, WSrc ws, Grid g, const View* __restrict__ Vp,
            float* __restrict__ fpad, int* __restrict__ box_out) {
     if (ws.phase && *ws.phase >= PH_STOP) return;
@@ -131,7 +141,7 @@ k_warp_pca(const T* __restrict__ f0, const T* __restrict__ mean,
             float o[4];
 #pragma unroll
             for (int e = 0; e < 4; e++) {
-                o[e] = tri_dense(f0, g, fmaf(x[0][e], g.inv_sx, (float)(i + e)),
+                o[e] = tri_halo(f0h, g, fmaf(x[0][e], g.inv_sx, (float)(i + e)),
                                  fmaf(x[1][e], g.inv_sy, (float)j), fmaf(x[2][e], g.inv_sz, (float)k));
                 if (o[e] != 0.0f) {
                     if (swp) box_add(b, j, i + e, k);
@@ -155,7 +165,7 @@ k_warp_pca(const T* __restrict__ f0, const T* __restrict__ mean,
                 for (int kk = 0; kk < K; kk++) v = fmaf(s_w[kk], ldg_f(U + ((long)kk * 3 + c) * N + n), v);
                 x[c] = v;
             }
-            const float o = tri_dense(f0, g, fmaf(x[0], g.inv_sx, (float)i), fmaf(x[1], g.inv_sy, (float)j),
+            const float o = tri_halo(f0h, g, fmaf(x[0], g.inv_sx, (float)i), fmaf(x[1], g.inv_sy, (float)j),
                                       fmaf(x[2], g.inv_sz, (float)k));
             if (swp) {
                 if (o != 0.0f) box_add(b, j, i, k);
@@ -177,7 +187,7 @@ k_warp_pca(const T* __restrict__ f0, const T* __restrict__ mean,
 // buffer and f_4 in the one-volume buffer, zero-halo layout.
 template <typename T, int KT>
 __global__ void __launch_bounds__(kWarpThreads)
-k_warp_batch(const T* __restrict__ f0, const T* __restrict__ mean,
+k_warp_batch(const float* __restrict__ f0h, const T* __restrict__ mean,
              const T* __restrict__ U, const SolveState* st, Grid g, const View* __restrict__ Vp,
              float4* __restrict__ fpad4, float* __restrict__ fpad, int* __restrict__ box_out) {
     if (st->phase >= PH_STOP || st->nvalid < 1) return;    // same gate as the batch projector
@@ -221,7 +231,7 @@ k_warp_batch(const T* __restrict__ f0, const T* __restrict__ mean,
         float o[TRIAL_BATCH];
 #pragma unroll
         for (int b = 0; b < TRIAL_BATCH; b++)
-            o[b] = tri_dense(f0, g, fmaf(x[b][0], g.inv_sx, (float)i), fmaf(x[b][1], g.inv_sy, (float)j),
+            o[b] = tri_halo(f0h, g, fmaf(x[b][0], g.inv_sx, (float)i), fmaf(x[b][1], g.inv_sy, (float)j),
                              fmaf(x[b][2], g.inv_sz, (float)k));
         const int a0 = swp ? j : i, a1 = swp ? i : j;
         const long d = pad_index(pd, a0, a1, k);
@@ -265,11 +275,10 @@ cudaError_t pca_dvf_t(const void* mean, const void* U, int K, const float* w, Gr
 }
 
 template <typename T>
-cudaError_t warp_pca_t(const void* f0, const void* mean, const void* U, int K, WSrc w, Grid g,
+cudaError_t warp_pca_t(const float* f, const void* mean, const void* U, int K, WSrc w, Grid g,
                        const View* Vd, float* fpad, int* box, cudaStream_t s) {
     const unsigned a = sizeof(T) * 4;
     bool vec = (g.nx % 4 == 0) && aligned(mean, a) && aligned(U, a) && aligned(fpad, 16);
-    const T* f = static_cast<const T*>(f0);
     const T* m = static_cast<const T*>(mean);
     const T* u = static_cast<const T*>(U);
     const RowLaunch L = row_launch(g, vec ? 4 : 1);
@@ -279,7 +288,7 @@ cudaError_t warp_pca_t(const void* f0, const void* mean, const void* U, int K, W
 }
 
 template <typename T>
-cudaError_t warp_batch_t(const T* f0, const T* mean, const T* U, int K, const SolveState* st, Grid g,
+cudaError_t warp_batch_t(const float* f0, const T* mean, const T* U, int K, const SolveState* st, Grid g,
                          const View* Vd, float4* fpad4, float* fpad, int* box, const RowLaunch& L,
                          cudaStream_t s) {
     switch (K) {
@@ -315,17 +324,23 @@ cudaError_t launch_warp_dvf(const void* f0, int dt, const float* dvf, Grid g, fl
                           cudaGetLastError()))
 }
 
-cudaError_t launch_warp_pca(const void* f0, const void* mean, const void* U, int dt, int K, WSrc w,
+cudaError_t launch_fill_f0h(const void* f0, int dt, Grid g, float* f0h, cudaStream_t s) {
+    const RowLaunch L = row_launch(g, 1);
+    PCAS_DT_DISPATCH(dt, (k_fill_f0h<T><<<L.grid, L.threads, 0, s>>>(static_cast<const T*>(f0), g, f0h),
+                          cudaGetLastError()))
+}
+
+cudaError_t launch_warp_pca(const float* f0, const void* mean, const void* U, int dt, int K, WSrc w,
                             Grid g, const View* Vd, float* fpad, int* box, cudaStream_t s) {
     PCAS_DT_DISPATCH(dt, (warp_pca_t<T>(f0, mean, U, K, w, g, Vd, fpad, box, s)))
 }
 
-cudaError_t launch_warp_batch(const void* f0, const void* mean, const void* U, int dt, int K,
+cudaError_t launch_warp_batch(const float* f0, const void* mean, const void* U, int dt, int K,
                               const SolveState* st, Grid g, const View* Vd, float4* fpad4, float* fpad,
                               cudaStream_t s) {
     const RowLaunch L = row_launch(g, 1);
     int* box = const_cast<int*>(st->box[1]);
-    PCAS_DT_DISPATCH(dt, (warp_batch_t<T>(static_cast<const T*>(f0), static_cast<const T*>(mean),
+    PCAS_DT_DISPATCH(dt, (warp_batch_t<T>(f0, static_cast<const T*>(mean),
                                           static_cast<const T*>(U), K, st, g, Vd, fpad4, fpad, box, L, s)))
 }
 

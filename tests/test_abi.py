@@ -62,7 +62,8 @@ def test_workspace_bytes_host_only(lib):
     npad = (((256 + 6) + 3) // 4 * 4) * 260 * 104          # two-voxel zero halo
     M = 512 * 384
     cap = 32 * 32 * 25 * 256                                 # 8x8x4 tiles of the Jacobian compaction
-    need = npad * (4 + 16) + M * (6 * 4 + 32) + cap * (4 + 4 * 3)   # f (+ 5th candidate), 4 candidates, 6 projections,
+    f0h = 262 * 262 * 106 * 4                                # reference CT with a three-voxel zero halo
+    need = f0h + npad * (4 + 16) + M * (6 * 4 + 32) + cap * (4 + 4 * 3)   # f (+ 5th candidate), 4 candidates, 6 projections,
     assert need <= n < need + 2_000_000 and n % 256 == 0            # ray table, compacted voxels
     assert P.workspace_bytes(vol, cb, 0) == 0 and P.workspace_bytes(vol, cb, 9) == 0
     # room for the y-fastest layout too: a non-square grid takes the larger of the two
