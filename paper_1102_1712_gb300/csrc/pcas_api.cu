@@ -477,7 +477,7 @@ int eval_gradient_pipeline(const void* f0, const void* mean, const void* U, int 
     PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, W.view, 1, W.rayt, W.st, W.part_res, s));
     PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
                 launch_adjoint_grad(W.rayt, g, W.view, W.f0h, mean, U, dt, K, step_setup, W.st, W.part_adj, W.adj,
-                                    T.vt, gather_blocks(T), 0ull, 0, s));
+                                    T.vt, gather_blocks(T), 0ull, 0, nullptr, s));
     return PCAS_OK;
 }
 
@@ -507,7 +507,7 @@ int solve_host(const void* f0, const void* mean, const void* U, int dtype, int K
         PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, W.view, it == 0, W.rayt, W.st, W.part_res, s));
         PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
                     launch_adjoint_grad(W.rayt, g, W.view, W.f0h, mean, U, dtype, K, 1, W.st, W.part_adj, W.adj, T.vt,
-                                        adj_blocks, 0ull, 0, s));
+                                        adj_blocks, 0ull, 0, nullptr, s));
         // Armijo backtracking over the schedule mu0, beta mu0, ...: the next (up
         // to five) step sizes that the rule may still try are rendered and
         // tested in one pass; the device accepts the first that passes, in
@@ -775,7 +775,7 @@ int cost_grad_f0(const float* f0, const float* mean, const float* U, int K, cons
     if (dJdw)
         PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
                     launch_adjoint_grad(W.rayt, g, W.view, W.f0h, mean, U, DT_F32, K, 0, W.st, W.part_adj, W.adj,
-                                        T.vt, gather_blocks(T), 0ull, 0, s));
+                                        T.vt, gather_blocks(T), 0ull, 0, nullptr, s));
     if (dJdf0)
         PCAS_LAUNCH(PCAS_K_GRAD_F0, s, launch_grad_f0(W.rayt, g, W.view, mean, U, K, W.st, z, zmax, acc, dJdf0, s));
     SolveState h;
@@ -1331,7 +1331,29 @@ size_t solver_extra(const pcas_cb* cb) {
 
 // Captures one device-driven solve into `graph` as an independent branch
 // (optionally preceded by a copy of the measured image from y_src).
+// A second capture stream and the two events of the residual branch (freed on
+// every path out of capture_solve).
+struct SideBranch {
+    cudaStream_t cs2 = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaError_t init() {
+        cudaError_t e = cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+        return e;
+    }
+    ~SideBranch() {
+        if (join) cudaEventDestroy(join);
+        if (fork) cudaEventDestroy(fork);
+        if (cs2) cudaStreamDestroy(cs2);
+    }
+};
+
 int capture_solve(pcas_solver s, cudaGraph_t graph, cudaStream_t cs, const float* y_src) {
+    SideBranch side;
+    if (side.init() != cudaSuccess) return fail(PCAS_ERR_CUDA, "graph build: stream/event creation failed");
+    cudaStream_t cs2 = side.cs2;
+    cudaEvent_t ev_fork = side.fork, ev_join = side.join;
     const Grid g = make_grid(&s->vol);
     const Ws& W = s->W;
     const View& V = s->view0;
@@ -1360,9 +1382,13 @@ int capture_solve(pcas_solver s, cudaGraph_t graph, cudaStream_t cs, const float
     // one iteration: residual + gradient, then the candidate batches
     PCAS_G(cudaGraphConditionalHandleCreate(&s->h_inner, outer_body, 0, cudaGraphCondAssignDefault));
     PCAS_G(cudaStreamBeginCaptureToGraph(cs, outer_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    PCAS_G(launch_resid(W.pbuf, s->y, V, W.view, -1, W.rayt, W.st, W.part_res, cs));
+    // residual (ray table) on a side branch beside the Jacobian pass; the gather joins both
+    PCAS_G(cudaEventRecord(ev_fork, cs));
+    PCAS_G(cudaStreamWaitEvent(cs2, ev_fork, 0));
+    PCAS_G(launch_resid(W.pbuf, s->y, V, W.view, -1, W.rayt, W.st, W.part_res, cs2));
+    PCAS_G(cudaEventRecord(ev_join, cs2));
     PCAS_G(launch_adjoint_grad(W.rayt, g, W.view, W.f0h, s->mean, s->U, s->dtype, s->K, 1, W.st, W.part_adj,
-                               W.adj, s->tune.vt, gather_blocks(s->tune), s->h_inner, 1, cs));
+                               W.adj, s->tune.vt, gather_blocks(s->tune), s->h_inner, 1, ev_join, cs));
     cudaGraph_t inner_body;
     PCAS_TRY(add_while(cs, s->h_inner, &inner_body));
     k_ctrl_iter_end<<<1, 1, 0, cs>>>(W.st, s->h_outer);

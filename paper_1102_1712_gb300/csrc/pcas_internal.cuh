@@ -531,10 +531,12 @@ struct AdjScratch {
 };
 // hbatch / use_h: inside a device-driven solve the gradient's last block opens
 // (or not) the iteration's candidate-batch loop by setting this handle.
+// join (may be null): an event the gather waits for (the residual pass, which
+// the Jacobian pass does not need, can then run beside it on another stream).
 cudaError_t launch_adjoint_grad(const float4* rayt, Grid g, const View* V, const float* f0h,
                                 const void* mean, const void* U, int dt, int K, int step_setup,
                                 SolveState* st, double* part, const AdjScratch& as, int vt, int max_blocks,
-                                unsigned long long hbatch, int use_h, cudaStream_t s);
+                                unsigned long long hbatch, int use_h, cudaEvent_t join, cudaStream_t s);
 // dJ/df0 = W^T (2 P^T r): z (N floats) and acc (N 64-bit) are scratch,
 // zmax_bits one word; out (N floats) receives the gradient.
 cudaError_t launch_grad_f0(const float4* rayt, Grid g, const View* V, const float* mean, const float* U,
