@@ -36,7 +36,7 @@ def _rank(rank, ws, port, out):
 def test_max_over_two_gloo_ranks():
     ws = 2
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.start_processes(_rank, args=(ws, port, out), nprocs=ws, start_method="spawn", join=True)
         got = dict(out)
