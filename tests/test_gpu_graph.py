@@ -133,9 +133,9 @@ def test_layout_follows_the_angle(P):
 @pytest.mark.parametrize("mu_min,max_trials", [(0.04, 30), (0.0, 7), (0.0, 6), (0.0, 1), (0.011, 4)])
 def test_partial_batches_and_single_trials(P, mu_min, max_trials):
     """Schedules that fill a batch of five only partly (mu_min cuts it to 3 or
-    4 steps, max_trials leaves 2 or 1) and the one-candidate pass: host loop and
-    device-driven graph agree bitwise, and both follow the oracle's one-at-a-time
-    rule."""
+    4 steps, max_trials leaves 2 or 1, down to batches of one step): host loop
+    and device-driven graph agree bitwise, and both follow the oracle's
+    one-at-a-time rule."""
     pb = tiny_problem()
     d = to_dev(pb)
     prm = P.default_params(pb["step"], mu_min=mu_min, max_iter=12, max_trials=max_trials)
