@@ -283,30 +283,37 @@ int lp_predict(const double* hist, const double* c, int K, int L, double* w0);
  *   voxel_tile        voxel tile of the gradient pass: 0 = 8x8x4, 1 = 16x4x4,
  *                     2 = 32x4x2, 3 = 16x8x2, 4 = 32x8x1, 5 = 64x4x1
  *   gather_per_sm     blocks of the gradient gather per SM (1..26)
+ *   skip_empty        empty-space skipping of the solver projectors (0 or 1):
+ *                     the warp kernels mark the 8x8x8-voxel bricks holding
+ *                     non-zero voxels, and each ray's samples are cut to the
+ *                     span from its first to its last sample whose cell lies
+ *                     in a marked brick.  Exact: the samples left out
+ *                     interpolate eight zero voxels, so every sum is bitwise
+ *                     the same either way
  * and per 22.5-degree bin of the gantry angle modulo 180 degrees (bin b is
  * centred on 22.5 b degrees):
  *   ray_lw4[b]        patch width of the batch projector (2..4)
  *   chunk[b]          its sample indices per shared-memory chunk (even, 2..64)
  *   swap[b]           layout of the solver volumes: 0 = x fastest,
  *                     1 = y fastest
- * Every call takes the entry of its bucket, or the defaults (3, 0, 0, 8; per
- * bin 3, 16, y fastest in bins 3..5) when there is none; a device-driven
+ * Every call takes the entry of its bucket, or the defaults (3, 0, 0, 8, 1;
+ * per bin 3, 16, y fastest in bins 3..5) when there is none; a device-driven
  * solver takes the entry in force when it is created (the per-bin shapes
  * follow the angle of each solve).  Other shapes reorder floating-point sums:
  * results can differ by rounding between shapes, and are reproducible for a
  * fixed table. */
 typedef struct {
-    int ray_lw1, chunk1, voxel_tile, gather_per_sm;
+    int ray_lw1, chunk1, voxel_tile, gather_per_sm, skip_empty;
     unsigned char ray_lw4[8], chunk[8], swap[8];
 } pcas_tuning;
 
 /* Measures shapes on this problem and stores the fastest in its bucket:
  * trial solves (solve_projection with max_iter capped at 3, from w_init, at
- * the centre angle of a bin), every kernel timed with CUDA events: per bin
- * the layouts, then per bin the patch width and chunk of the four-candidate
- * projector, then the one-volume projector's width and chunk, the voxel tile
- * and the gather size, each chosen by the time of the kernels it drives
- * (about 130 trial solves).  f0, mean, U, y, ws: device, as solve_projection
+ * the centre angle of a bin), every kernel timed with CUDA events: empty-
+ * space skipping on or off, then per bin the layout, then per bin the patch
+ * width and chunk of the five-candidate projector, then the one-volume
+ * projector's width and chunk, the voxel tile and the gather size, each
+ * chosen by the time of the kernels it drives (about 140 trial solves).  f0, mean, U, y, ws: device, as solve_projection
  * (ws of pcas_workspace_bytes); w_init: host, K doubles or NULL (zeros);
  * out (host, may be NULL) receives the stored entry.  Synchronous.  Bins
  * whose view is invalid (volume not in front of the source) keep their

@@ -191,8 +191,8 @@ int check_model(const void* mean, const void* U, int K) {
 
 // ------------------------------------------------------------- workspace
 struct Layout {
-    size_t state, view, f0h, fpad, fpad4, pbuf, rayt, part_drr, part_res, part_adj, act_idx, act_h, tile_count,
-        tile_off, total;
+    size_t state, view, f0h, f0m, fpad, fpad4, occ, pbuf, rayt, part_drr, part_res, part_adj, act_idx, act_h,
+        tile_count, tile_off, total;
 };
 
 Layout layout(const pcas_vol* vol, const pcas_cb* cb, int K) {
@@ -206,8 +206,10 @@ Layout layout(const pcas_vol* vol, const pcas_cb* cb, int K) {
     L.state = off; off += align256(sizeof(SolveState));
     L.view = off; off += align256(sizeof(View));
     L.f0h = off; off += align256((size_t)f0h_count(vol->nx, vol->ny, vol->nz) * sizeof(float));  // f0, halo 3
+    L.f0m = off; off += align256((size_t)occ_count(vol->nx, vol->ny, vol->nz));     // its bricks (zeroed with it)
     L.fpad = off; off += align256(npad * sizeof(float));                 // f(w), zero halo
     L.fpad4 = off; off += align256(npad * sizeof(float4));               // candidates 0-3 (4 in fpad)
+    L.occ = off; off += align256((size_t)occ_count(vol->nx, vol->ny, vol->nz) * sizeof(unsigned int));
     L.pbuf = off; off += align256((size_t)NBUF * M * sizeof(float));     // projection ring
     L.rayt = off; off += align256(2 * M * sizeof(float4));               // (step, r), (1/step, 0)
     L.part_drr = off; off += align256((size_t)drr_blocks(cb->nu, cb->nv) * DRR_PART_VALS * sizeof(double));
@@ -226,7 +228,9 @@ struct Ws {
     SolveState* st;
     View* view;
     float* f0h;
-    size_t f0h_bytes;
+    unsigned char* f0m;       // bricks of the reference CT, right after f0h
+    size_t f0h_bytes;         // f0h and f0m
+    unsigned int* occ;        // occupancy bricks of the solver volumes
     float *fpad, *pbuf;
     float4 *fpad4, *rayt;
     double *part_drr, *part_res, *part_adj;
@@ -244,9 +248,11 @@ int bind_ws(void* ws, size_t ws_bytes, const pcas_vol* vol, const pcas_cb* cb, i
     W->st = reinterpret_cast<SolveState*>(b + L.state);
     W->view = reinterpret_cast<View*>(b + L.view);
     W->f0h = reinterpret_cast<float*>(b + L.f0h);
+    W->f0m = reinterpret_cast<unsigned char*>(b + L.f0m);
     W->f0h_bytes = L.fpad - L.f0h;
     W->fpad = reinterpret_cast<float*>(b + L.fpad);
     W->fpad4 = reinterpret_cast<float4*>(b + L.fpad4);
+    W->occ = reinterpret_cast<unsigned int*>(b + L.occ);
     W->pbuf = reinterpret_cast<float*>(b + L.pbuf);
     W->rayt = reinterpret_cast<float4*>(b + L.rayt);
     W->part_drr = reinterpret_cast<double*>(b + L.part_drr);
@@ -257,21 +263,27 @@ int bind_ws(void* ws, size_t ws_bytes, const pcas_vol* vol, const pcas_cb* cb, i
     W->adj.tile_count = reinterpret_cast<int*>(b + L.tile_count);
     W->adj.tile_off = reinterpret_cast<int*>(b + L.tile_off);
     W->fpad_bytes = L.fpad4 - L.fpad;
-    W->fpad4_bytes = L.pbuf - L.fpad4;
+    W->fpad4_bytes = L.occ - L.fpad4;
     return PCAS_OK;
+}
+
+// Occupancy bricks as the solver kernels take them (skipping off: none).
+inline Occ occ_of(const Ws& W, const Tune& T) {
+    return Occ{T.skip ? W.occ : nullptr, &W.st->occ_gen, T.skip ? W.f0m : nullptr};
 }
 
 // ------------------------------------------------------------ launch shapes
 // Default shapes: 8 x 4 warp patches, 16-sample chunks for the batch
 // projector (the one-volume projector marches through L1), 8 x 8 x 4 voxel tiles,
-// eight gather blocks per SM, y-fastest solver volumes for angles near 90
-// (bins 67.5 ... 112.5 degrees).
+// eight gather blocks per SM, empty-space skipping on, y-fastest solver
+// volumes for angles near 90 (bins 67.5 ... 112.5 degrees).
 Tune default_tune() {
     Tune T;
     T.lw1 = 3;
     T.chunk1 = 0;
     T.vt = 0;
     T.adj_mult = 8;
+    T.skip = 1;
     for (int b = 0; b < NBIN; b++) {
         T.lw4[b] = 3;
         T.chunk4[b] = 16;
@@ -455,10 +467,11 @@ int check_finite(const double* v, int n, const char* name) {
         if (rc_ != PCAS_OK) return rc_; \
     } while (0)
 
-// The halo copy of the reference CT for this call (zeroed, then filled).
-int stage_f0h(const void* f0, int dt, const Grid& g, const Ws& W, cudaStream_t s) {
+// The halo copy of the reference CT for this call and its bricks (zeroed,
+// then filled).
+int stage_f0h(const void* f0, int dt, const Grid& g, const Ws& W, const Tune& T, cudaStream_t s) {
     PCAS_CUDA(cudaMemsetAsync(W.f0h, 0, W.f0h_bytes, s));
-    PCAS_LAUNCH(PCAS_K_INIT, s, launch_fill_f0h(f0, dt, g, W.f0h, s));
+    PCAS_LAUNCH(PCAS_K_INIT, s, launch_fill_f0h(f0, dt, g, W.f0h, T.skip ? W.f0m : nullptr, s));
     return PCAS_OK;
 }
 
@@ -470,14 +483,16 @@ int eval_gradient_pipeline(const void* f0, const void* mean, const void* U, int 
     WSrc ws{};
     ws.dev = W.st->w;
     ws.phase = &W.st->phase;
-    PCAS_TRY(stage_f0h(f0, dt, g, W, s));
-    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(W.f0h, mean, U, dt, K, ws, g, W.view, W.fpad, W.st->box[0], s));
+    PCAS_TRY(stage_f0h(f0, dt, g, W, T, s));
+    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(W.f0h, mean, U, dt, K, ws, g, W.view, W.fpad, W.st->box[0],
+                                                    occ_of(W, T), s));
     PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
-                launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, T, 0ull, 0, s));
+                launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, T, 0ull, 0,
+                                  occ_of(W, T), s));
     PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, W.view, 1, W.rayt, W.st, W.part_res, s));
     PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
-                launch_adjoint_grad(W.rayt, g, W.view, W.f0h, mean, U, dt, K, step_setup, W.st, W.part_adj, W.adj,
-                                    T.vt, gather_blocks(T), 0ull, 0, nullptr, s));
+                launch_adjoint_grad(W.rayt, g, W.view, W.f0h, occ_of(W, T).f0m, mean, U, dt, K, step_setup, W.st,
+                                    W.part_adj, W.adj, T.vt, gather_blocks(T), 0ull, 0, nullptr, s));
     return PCAS_OK;
 }
 
@@ -498,16 +513,18 @@ int solve_host(const void* f0, const void* mean, const void* U, int dtype, int K
     WSrc wcur{};
     wcur.dev = W.st->w;
     wcur.phase = &W.st->phase;
-    PCAS_TRY(stage_f0h(f0, dtype, g, W, s));
-    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(W.f0h, mean, U, dtype, K, wcur, g, W.view, W.fpad, W.st->box[0], s));
+    PCAS_TRY(stage_f0h(f0, dtype, g, W, T, s));
+    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(W.f0h, mean, U, dtype, K, wcur, g, W.view, W.fpad,
+                                                    W.st->box[0], occ_of(W, T), s));
     PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
-                launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, T, 0ull, 0, s));
+                launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, T, 0ull, 0,
+                                  occ_of(W, T), s));
     int iters = 0, phase = PH_RUNNING;
     for (int it = 0; it < prm->max_iter; it++) {
         PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, W.view, it == 0, W.rayt, W.st, W.part_res, s));
         PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
-                    launch_adjoint_grad(W.rayt, g, W.view, W.f0h, mean, U, dtype, K, 1, W.st, W.part_adj, W.adj, T.vt,
-                                        adj_blocks, 0ull, 0, nullptr, s));
+                    launch_adjoint_grad(W.rayt, g, W.view, W.f0h, occ_of(W, T).f0m, mean, U, dtype, K, 1, W.st,
+                                        W.part_adj, W.adj, T.vt, adj_blocks, 0ull, 0, nullptr, s));
         // Armijo backtracking over the schedule mu0, beta mu0, ...: the next (up
         // to five) step sizes that the rule may still try are rendered and
         // tested in one pass; the device accepts the first that passes, in
@@ -529,10 +546,11 @@ int solve_host(const void* f0, const void* mean, const void* U, int dtype, int K
                 if (phase == PH_RUNNING) phase = PH_STOP;
                 break;
             }
-            PCAS_LAUNCH(PCAS_K_WARP_BATCH, s, launch_warp_batch(W.f0h, mean, U, dtype, K, W.st, g, W.view, W.fpad4, W.fpad, s));
+            PCAS_LAUNCH(PCAS_K_WARP_BATCH, s, launch_warp_batch(W.f0h, mean, U, dtype, K, W.st, g, W.view,
+                                                                W.fpad4, W.fpad, occ_of(W, T), s));
             PCAS_LAUNCH(PCAS_K_DRR_BATCH, s,
                         launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, TRIAL_BATCH, W.st, W.part_drr,
-                                          T, 0ull, 0, s));
+                                          T, 0ull, 0, occ_of(W, T), s));
             PCAS_CUDA(cudaMemcpyAsync(&phase, &W.st->phase, sizeof(int), cudaMemcpyDeviceToHost, s));
             PCAS_CUDA(cudaStreamSynchronize(s));
             if (phase != PH_RUNNING) break;
@@ -767,15 +785,17 @@ int cost_grad_f0(const float* f0, const float* mean, const float* U, int K, cons
     WSrc wsrc{};
     wsrc.dev = W.st->w;
     wsrc.phase = &W.st->phase;
-    PCAS_TRY(stage_f0h(f0, DT_F32, g, W, s));
-    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(W.f0h, mean, U, DT_F32, K, wsrc, g, W.view, W.fpad, W.st->box[0], s));
+    PCAS_TRY(stage_f0h(f0, DT_F32, g, W, T, s));
+    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(W.f0h, mean, U, DT_F32, K, wsrc, g, W.view, W.fpad,
+                                                    W.st->box[0], occ_of(W, T), s));
     PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
-                launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, T, 0ull, 0, s));
+                launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, T, 0ull, 0,
+                                  occ_of(W, T), s));
     PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, W.view, 1, W.rayt, W.st, W.part_res, s));
     if (dJdw)
         PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
-                    launch_adjoint_grad(W.rayt, g, W.view, W.f0h, mean, U, DT_F32, K, 0, W.st, W.part_adj, W.adj,
-                                        T.vt, gather_blocks(T), 0ull, 0, nullptr, s));
+                    launch_adjoint_grad(W.rayt, g, W.view, W.f0h, occ_of(W, T).f0m, mean, U, DT_F32, K, 0, W.st,
+                                        W.part_adj, W.adj, T.vt, gather_blocks(T), 0ull, 0, nullptr, s));
     if (dJdf0)
         PCAS_LAUNCH(PCAS_K_GRAD_F0, s, launch_grad_f0(W.rayt, g, W.view, mean, U, K, W.st, z, zmax, acc, dJdf0, s));
     SolveState h;
@@ -826,6 +846,7 @@ namespace {
 pcas_tuning to_public(const Tune& T) {
     pcas_tuning t;
     t.ray_lw1 = T.lw1; t.chunk1 = T.chunk1; t.voxel_tile = T.vt; t.gather_per_sm = T.adj_mult;
+    t.skip_empty = T.skip;
     for (int b = 0; b < NBIN; b++) {
         t.ray_lw4[b] = T.lw4[b]; t.chunk[b] = T.chunk4[b]; t.swap[b] = T.swap[b];
     }
@@ -835,13 +856,15 @@ pcas_tuning to_public(const Tune& T) {
 int from_public(const pcas_tuning* t, Tune* T) {
     if (!t) return fail(PCAS_ERR_INVALID_ARG, "tuning is NULL");
     if (t->ray_lw1 < 2 || t->ray_lw1 > 4 || t->chunk1 < 0 || t->chunk1 > 128 || (t->chunk1 & 1) ||
-        t->voxel_tile < 0 || t->voxel_tile >= NVOXTILE || t->gather_per_sm < 1 || t->gather_per_sm > 26)
+        t->voxel_tile < 0 || t->voxel_tile >= NVOXTILE || t->gather_per_sm < 1 || t->gather_per_sm > 26 ||
+        t->skip_empty < 0 || t->skip_empty > 1)
         return fail(PCAS_ERR_INVALID_ARG, "tuning field out of range");
     for (int b = 0; b < NBIN; b++)
         if (t->ray_lw4[b] < 2 || t->ray_lw4[b] > 4 || t->chunk[b] < 2 || t->chunk[b] > 64 || (t->chunk[b] & 1) ||
             t->swap[b] > 1)
             return fail(PCAS_ERR_INVALID_ARG, "tuning field of angle bin %d out of range", b);
     T->lw1 = t->ray_lw1; T->chunk1 = t->chunk1; T->vt = t->voxel_tile; T->adj_mult = t->gather_per_sm;
+    T->skip = t->skip_empty;
     for (int b = 0; b < NBIN; b++) {
         T->lw4[b] = t->ray_lw4[b]; T->chunk4[b] = t->chunk[b]; T->swap[b] = t->swap[b];
     }
@@ -923,22 +946,7 @@ int pcas_autotune(const void* f0, const void* mean, const void* U, int dtype, in
     double a[PCAS_K_COUNT];
     int rc = PCAS_OK;
     bool ok_bin[NBIN];
-    // 1. per angle bin, the layout of the solver volumes, judged by every warp
-    //    and projector kernel together (they write and read the same buffers)
-    for (int b = 0; b < NBIN && rc == PCAS_OK; b++) {
-        double tt[2] = {0, 0};
-        ok_bin[b] = true;
-        for (int sw = 0; sw < 2 && ok_bin[b]; sw++) {
-            Tune X = best;
-            X.swap[b] = (unsigned char)sw;
-            const int r = tr.run(X, b, a);
-            if (r == PCAS_ERR_INVALID_ARG) { ok_bin[b] = false; break; }   // view invalid at this angle
-            if (r != PCAS_OK) { rc = r; break; }
-            tt[sw] = a[PCAS_K_WARP_PCA] + a[PCAS_K_DRR_SOLVER] + 2.0 * (a[PCAS_K_WARP_BATCH] + a[PCAS_K_DRR_BATCH]);
-        }
-        if (rc != PCAS_OK || !ok_bin[b]) continue;
-        best.swap[b] = tt[1] < tt[0] ? 1 : 0;
-    }
+    for (int b = 0; b < NBIN; b++) ok_bin[b] = true;
     const int probe[4] = {0, 2, 4, 6};
     auto sweep = [&](auto apply, const int* cands, int ncand, const int* kinds, int nkinds, const int* bins,
                      int nbins, int* choice) -> int {
@@ -951,6 +959,7 @@ int pcas_autotune(const void* f0, const void* mean, const void* U, int dtype, in
             for (int q = 0; q < nbins; q++) {
                 if (!ok_bin[bins[q]]) continue;
                 const int r = tr.run(X, bins[q], a);
+                if (r == PCAS_ERR_INVALID_ARG) { ok_bin[bins[q]] = false; continue; }   // view invalid here
                 if (r != PCAS_OK) return r;
                 for (int k = 0; k < nkinds; k++) t += a[kinds[k]];
                 used++;
@@ -962,6 +971,31 @@ int pcas_autotune(const void* f0, const void* mean, const void* U, int dtype, in
         }
         return PCAS_OK;
     };
+    // 0. empty-space skipping, judged by the warps (which mark the bricks) and
+    //    the projectors (which walk them)
+    {
+        const int onoff[2] = {1, 0};
+        const int kw[4] = {PCAS_K_WARP_PCA, PCAS_K_DRR_SOLVER, PCAS_K_WARP_BATCH, PCAS_K_DRR_BATCH};
+        int c = best.skip;
+        rc = sweep([](Tune& X, int v) { X.skip = v; }, onoff, 2, kw, 4, probe, 4, &c);
+        best.skip = c;
+        for (int b = 0; b < NBIN; b++) ok_bin[b] = true;
+    }
+    // 1. per angle bin, the layout of the solver volumes, judged by every warp
+    //    and projector kernel together (they write and read the same buffers)
+    for (int b = 0; b < NBIN && rc == PCAS_OK; b++) {
+        double tt[2] = {0, 0};
+        for (int sw = 0; sw < 2 && ok_bin[b]; sw++) {
+            Tune X = best;
+            X.swap[b] = (unsigned char)sw;
+            const int r = tr.run(X, b, a);
+            if (r == PCAS_ERR_INVALID_ARG) { ok_bin[b] = false; break; }   // view invalid at this angle
+            if (r != PCAS_OK) { rc = r; break; }
+            tt[sw] = a[PCAS_K_WARP_PCA] + a[PCAS_K_DRR_SOLVER] + 2.0 * (a[PCAS_K_WARP_BATCH] + a[PCAS_K_DRR_BATCH]);
+        }
+        if (rc != PCAS_OK || !ok_bin[b]) continue;
+        best.swap[b] = tt[1] < tt[0] ? 1 : 0;
+    }
     // 2. per angle bin, the patch width and chunk of the batch projector
     for (int b = 0; b < NBIN && rc == PCAS_OK; b++) {
         if (!ok_bin[b]) continue;
@@ -1366,13 +1400,14 @@ int capture_solve(pcas_solver s, cudaGraph_t graph, cudaStream_t cs, const float
     PCAS_G(cudaMemcpyAsync(s->d_init, s->h_init, sizeof(InitBlock), cudaMemcpyHostToDevice, cs));
     k_init_dev<<<1, 32, 0, cs>>>(W.st, s->d_init);
     PCAS_G(cudaGetLastError());
-    PCAS_G(launch_fill_f0h(s->f0, s->dtype, g, W.f0h, cs));     // f0 may change between solves
+    const Occ oc = occ_of(W, s->tune);
+    PCAS_G(launch_fill_f0h(s->f0, s->dtype, g, W.f0h, s->tune.skip ? W.f0m : nullptr, cs));  // f0 may change
     WSrc wcur{};
     wcur.dev = W.st->w;
     wcur.phase = &W.st->phase;
-    PCAS_G(launch_warp_pca(W.f0h, s->mean, s->U, s->dtype, s->K, wcur, g, W.view, W.fpad, W.st->box[0], cs));
+    PCAS_G(launch_warp_pca(W.f0h, s->mean, s->U, s->dtype, s->K, wcur, g, W.view, W.fpad, W.st->box[0], oc, cs));
     PCAS_G(launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, s->y, W.pbuf, 0, W.st, W.part_drr, s->tune, 0ull, 0,
-                             cs));
+                             oc, cs));
     k_ctrl_start<<<1, 1, 0, cs>>>(W.st, s->h_outer);
     PCAS_G(cudaGetLastError());
     cudaGraph_t outer_body;
@@ -1387,7 +1422,7 @@ int capture_solve(pcas_solver s, cudaGraph_t graph, cudaStream_t cs, const float
     PCAS_G(cudaStreamWaitEvent(cs2, ev_fork, 0));
     PCAS_G(launch_resid(W.pbuf, s->y, V, W.view, -1, W.rayt, W.st, W.part_res, cs2));
     PCAS_G(cudaEventRecord(ev_join, cs2));
-    PCAS_G(launch_adjoint_grad(W.rayt, g, W.view, W.f0h, s->mean, s->U, s->dtype, s->K, 1, W.st, W.part_adj,
+    PCAS_G(launch_adjoint_grad(W.rayt, g, W.view, W.f0h, oc.f0m, s->mean, s->U, s->dtype, s->K, 1, W.st, W.part_adj,
                                W.adj, s->tune.vt, gather_blocks(s->tune), s->h_inner, 1, ev_join, cs));
     cudaGraph_t inner_body;
     PCAS_TRY(add_while(cs, s->h_inner, &inner_body));
@@ -1397,9 +1432,9 @@ int capture_solve(pcas_solver s, cudaGraph_t graph, cudaStream_t cs, const float
     // one candidate batch: warp and projection; the projection's last block
     // decides the batch and whether another follows
     PCAS_G(cudaStreamBeginCaptureToGraph(cs, inner_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    PCAS_G(launch_warp_batch(W.f0h, s->mean, s->U, s->dtype, s->K, W.st, g, W.view, W.fpad4, W.fpad, cs));
+    PCAS_G(launch_warp_batch(W.f0h, s->mean, s->U, s->dtype, s->K, W.st, g, W.view, W.fpad4, W.fpad, oc, cs));
     PCAS_G(launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, s->y, W.pbuf, TRIAL_BATCH, W.st, W.part_drr,
-                             s->tune, s->h_inner, 1, cs));
+                             s->tune, s->h_inner, 1, oc, cs));
     PCAS_G(cudaStreamEndCapture(cs, &done));
     return PCAS_OK;
 }

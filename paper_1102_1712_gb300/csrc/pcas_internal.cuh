@@ -103,9 +103,45 @@ struct SolveState {
     // BOX_EMPTY everywhere.  Written by the warp kernels, read and reset by the
     // projector that consumes the volume.
     int box[2][6];
+    unsigned int occ_gen;                 // pass number of the occupancy bricks (never reset)
 };
 
 enum : int { BOX_EMPTY = 0x3fffffff };
+
+// ------------------------------------------------------ occupancy bricks
+// Empty-space skipping of the solver projectors (exact).  A sample of the
+// march whose cell has its (0,0,0) tap at c = floor(q) (frame voxel indices)
+// belongs to brick ((c_x + 1) >> 3, (c_y + 1) >> 3, (c_z + 1) >> 3), clamped to
+// the grid of (n >> 3) + 1 bricks per axis; its eight taps lie in
+// [8 b - 1, 8 b + 7] per axis.  The warp kernels mark every brick whose taps
+// include a non-zero voxel of the volumes they write with the current pass
+// number; the projector that reads those volumes treats a brick holding any
+// other number as empty: each of its samples interpolates eight zero taps and
+// adds exactly +0, so leaving such samples out of a ray changes no bit of the
+// sum.  Marks of earlier passes can only make the projector do more work, so
+// the mask is never cleared; the projector's last block advances the number.
+// The reference CT has bricks of its own (world axes, one byte each, 0 or 1):
+// k_fill_f0h marks them when it writes the halo copy, and the warp and
+// Jacobian kernels interpolate only in cells of marked bricks -- elsewhere all
+// eight taps are zero and so is the result (A.5) and its gradient (A.8).
+struct Occ {
+    unsigned int* mask;       // null: no marking and no skipping
+    unsigned int* gen;        // the pass number (SolveState::occ_gen)
+    const unsigned char* f0m; // bricks of the reference CT (null: none)
+};
+__host__ __device__ inline int occ_n(int n) { return (n >> 3) + 1; }
+__host__ __device__ inline long occ_count(int nx, int ny, int nz) {
+    return (long)occ_n(nx) * occ_n(ny) * occ_n(nz);
+}
+// Marks the bricks whose taps include a frame voxel of [x0, x1] x [y0, y1] x
+// {z}: voxel v is a tap of the cells of bricks v >> 3 and (v + 1) >> 3 along
+// each axis (two bricks where v + 1 is a multiple of 8).
+__device__ __forceinline__ void occ_mark(unsigned int* m, unsigned int gen, int nbx, int nby, int x0, int x1,
+                                         int y0, int y1, int z) {
+    for (int bz = z >> 3; bz <= (z + 1) >> 3; bz++)
+        for (int by = y0 >> 3; by <= (y1 + 1) >> 3; by++)
+            for (int bx = x0 >> 3; bx <= (x1 + 1) >> 3; bx++) m[((long)bz * nby + by) * nbx + bx] = gen;
+}
 
 // Number of the next (up to TRIAL_BATCH) step sizes mu, beta mu, ... that the
 // backtracking rule may still try: mu >= mu_min and fewer than max_trials
@@ -233,6 +269,19 @@ __device__ __forceinline__ void taps_halo(const float* __restrict__ f, const Gri
     v[6] = __ldg(b + sz + sy); v[7] = __ldg(b + sz + sy + 1);
 }
 
+// Brick of the reference CT holding the cell that taps_halo takes at q
+// (world axes, the same clamps and floors), as an index into its mask.
+__device__ __forceinline__ int f0_brick(const Grid& g, float qx, float qy, float qz) {
+    qx = fminf(fmaxf(qx, -2.0f), (float)g.nx + 1.0f);
+    qy = fminf(fmaxf(qy, -2.0f), (float)g.ny + 1.0f);
+    qz = fminf(fmaxf(qz, -2.0f), (float)g.nz + 1.0f);
+    const int nbx = occ_n(g.nx), nby = occ_n(g.ny), nbz = occ_n(g.nz);
+    const int bx = min(max(((int)floorf(qx) + 1) >> 3, 0), nbx - 1);
+    const int by = min(max(((int)floorf(qy) + 1) >> 3, 0), nby - 1);
+    const int bz = min(max(((int)floorf(qz) + 1) >> 3, 0), nbz - 1);
+    return (bz * nby + by) * nbx + bx;
+}
+
 // Eq. (A.5) from the halo copy: tri_dense's result without its branches.
 __device__ __forceinline__ float tri_halo(const float* __restrict__ f, const Grid& g, float qx, float qy,
                                           float qz) {
@@ -242,6 +291,14 @@ __device__ __forceinline__ float tri_halo(const float* __restrict__ f, const Gri
     const float c01 = fmaf(zx, v[5] - v[4], v[4]), c11 = fmaf(zx, v[7] - v[6], v[6]);
     const float c0 = fmaf(zy, c10 - c00, c00), c1 = fmaf(zy, c11 - c01, c01);
     return fmaf(zz, c1 - c0, c0);
+}
+
+// tri_halo, or +0 without touching the taps when the cell's brick of the
+// reference CT is empty (m: its bricks, or null).  The same bits either way.
+__device__ __forceinline__ float tri_halo_m(const float* __restrict__ f, const unsigned char* __restrict__ m,
+                                            const Grid& g, float qx, float qy, float qz) {
+    if (m && !__ldg(m + f0_brick(g, qx, qy, qz))) return 0.0f;
+    return tri_halo(f, g, qx, qy, qz);
 }
 
 // Same interpolant on the zero-halo layout: no bounds tests and no clamps.
@@ -422,6 +479,7 @@ struct Tune {
                               // 0: it marches through L1 (no staging)
     int vt;                   // voxel tile of the gradient pass (vox_tile)
     int adj_mult;             // gather blocks per SM
+    int skip;                 // empty-space skipping of the projectors (occupancy bricks)
     unsigned char lw4[NBIN];      // per angle bin: patch width of the batch projector,
     unsigned char chunk4[NBIN];   // its staged chunk,
     unsigned char swap[NBIN];     // and the layout of the solver volumes (solver_pad)
@@ -484,18 +542,20 @@ cudaError_t launch_pca_dvf(const void* mean, const void* U, int dt, int K, const
 cudaError_t launch_warp_dvf(const void* f0, int dt, const float* dvf, Grid g, float* f, cudaStream_t s);
 // Copies f0 (storage type dt) into the interior of the halo copy f0h (whose
 // halo the caller has zeroed; it is never written).
-cudaError_t launch_fill_f0h(const void* f0, int dt, Grid g, float* f0h, cudaStream_t s);
+// f0m (may be null): bricks of the reference CT, zeroed by the caller, marked here.
+cudaError_t launch_fill_f0h(const void* f0, int dt, Grid g, float* f0h, unsigned char* f0m, cudaStream_t s);
 // Solver warps: launch_warp_pca writes f(w_src) to the scalar zero-halo
 // buffer; launch_warp_batch writes the batch: candidates st->wt[0..3]
 // interleaved (float4) and wt[4] to fpad.
 // Vd (device, may be null): its swap selects the layout (solver_pad); the
 // bounding box is recorded in the same frame.
 // f0h: the halo copy of the reference CT (float); mean and U in storage type dt.
+// oc: occupancy bricks of the written volumes (oc.mask null: none).
 cudaError_t launch_warp_pca(const float* f0h, const void* mean, const void* U, int dt, int K, WSrc w,
-                            Grid g, const View* Vd, float* fpad, int* box, cudaStream_t s);
+                            Grid g, const View* Vd, float* fpad, int* box, Occ oc, cudaStream_t s);
 cudaError_t launch_warp_batch(const float* f0h, const void* mean, const void* U, int dt, int K,
                               const SolveState* st, Grid g, const View* Vd, float4* fpad4, float* fpad,
-                              cudaStream_t s);
+                              Occ oc, cudaStream_t s);
 cudaError_t launch_drr_plain(const float* f, Grid g, const View& V, float* p, cudaStream_t s);
 // Siddon geometry in double precision (world mm): source, unit axes, pixel
 // grid and the voxel grid (origin = centre of voxel (0,0,0)).
@@ -511,11 +571,13 @@ cudaError_t launch_drr_siddon(const float* f, const SidView& V, float* p, cudaSt
 // schedule).  Vh: the view on the host (grid size), Vd: the same in device
 // memory (read by the kernels, so captured launches stay view-independent).
 // hbatch / use_h: inside a device-driven solve the batch projector sets this
-// conditional handle to whether another candidate batch follows.
+// conditional handle to whether another candidate batch follows.  oc: the
+// occupancy bricks the warp kernels marked for these volumes (oc.mask null:
+// every ray keeps its box-clipped range).
 cudaError_t launch_drr_solver(const float* fpad, const float4* fpad4, Grid g,
                               const View& Vh, const View* Vd, const float* y, float* pbuf, int mode,
                               SolveState* st, double* part, const Tune& T, unsigned long long hbatch,
-                              int use_h, cudaStream_t s);
+                              int use_h, Occ oc, cudaStream_t s);
 cudaError_t launch_resid(const float* pbuf, const float* y, const View& Vh, const View* Vd, int first,
                          float4* rayt, SolveState* st, double* part, cudaStream_t s);
 cudaError_t launch_adjoint_plain(const float* img, Grid g, const View& V, float* gout,
@@ -533,8 +595,10 @@ struct AdjScratch {
 // (or not) the iteration's candidate-batch loop by setting this handle.
 // join (may be null): an event the gather waits for (the residual pass, which
 // the Jacobian pass does not need, can then run beside it on another stream).
+// f0m (may be null): bricks of the reference CT (see Occ).
 cudaError_t launch_adjoint_grad(const float4* rayt, Grid g, const View* V, const float* f0h,
-                                const void* mean, const void* U, int dt, int K, int step_setup,
+                                const unsigned char* f0m, const void* mean, const void* U, int dt, int K,
+                                int step_setup,
                                 SolveState* st, double* part, const AdjScratch& as, int vt, int max_blocks,
                                 unsigned long long hbatch, int use_h, cudaEvent_t join, cudaStream_t s);
 // dJ/df0 = W^T (2 P^T r): z (N floats) and acc (N 64-bit) are scratch,

@@ -99,26 +99,50 @@ k_warp_dvf(const T* __restrict__ f0, const float* __restrict__ dvf, Grid g, long
 // i = (blockIdx.x blockDim.x + threadIdx.x) V with V voxels per thread (no
 // index divisions; 32-bit voxel offsets, volumes have < 2^31 voxels).
 
-// The halo copy of the reference CT (see tri_halo): interior only.
+// The halo copy of the reference CT (see tri_halo): interior only.  With f0m
+// it marks the bricks whose taps include a non-zero voxel (see Occ): voxel i
+// is a tap of the cells of bricks i >> 3 and (i + 1) >> 3 along each axis.
 template <typename T>
 __global__ void __launch_bounds__(kWarpThreads)
-k_fill_f0h(const T* __restrict__ f0, Grid g, float* __restrict__ f0h) {
+k_fill_f0h(const T* __restrict__ f0, Grid g, float* __restrict__ f0h, unsigned char* __restrict__ f0m) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
     if (i >= g.nx) return;
     const long sy = g.nx + 2 * F0_HALO, sz = sy * (g.ny + 2 * F0_HALO);
-    f0h[(k + F0_HALO) * sz + (j + F0_HALO) * sy + (i + F0_HALO)] = ldg_f(f0 + ((long)k * g.ny + j) * g.nx + i);
+    const float v = ldg_f(f0 + ((long)k * g.ny + j) * g.nx + i);
+    f0h[(k + F0_HALO) * sz + (j + F0_HALO) * sy + (i + F0_HALO)] = v;
+    if (f0m && v != 0.0f) {
+        const int nbx = occ_n(g.nx), nby = occ_n(g.ny);
+        for (int bz = k >> 3; bz <= (k + 1) >> 3; bz++)
+            for (int by = j >> 3; by <= (j + 1) >> 3; by++)
+                for (int bx = i >> 3; bx <= (i + 1) >> 3; bx++) f0m[(bz * nby + by) * nbx + bx] = 1;
+    }
 }
 
-// Fused DVF synthesis + warp into the zero-halo layout used by the solver.
+// Occupancy bricks of the solver frame (see Occ): the frame exchanges x and y
+// when swp is set.
+struct OccFrame {
+    unsigned int* m;
+    unsigned int gen;
+    int nbx, nby;
+};
+__device__ __forceinline__ OccFrame occ_frame(const Occ& oc, const Grid& g, int swp) {
+    OccFrame o{oc.mask, 0u, occ_n(swp ? g.ny : g.nx), occ_n(swp ? g.nx : g.ny)};
+    if (oc.mask) o.gen = *oc.gen;
+    return o;
+}
+
+// Fused DVF synthesis + warp into the zero-halo layout used by the solver;
+// marks the occupancy bricks of its non-zero voxels.
 // VEC: 4 voxels per thread along x (nx % 4 == 0, 16-byte aligned model).
 template <bool VEC, typename T>
 __global__ void __launch_bounds__(kWarpThreads)
 k_warp_pca(const float* __restrict__ f0h, const T* __restrict__ mean,
            const T* __restrict__ U, int K, WSrc ws, Grid g, const View* __restrict__ Vp,
-           float* __restrict__ fpad, int* __restrict__ box_out) {
+           float* __restrict__ fpad, int* __restrict__ box_out, Occ occ) {
     if (ws.phase && *ws.phase >= PH_STOP) return;
     const int swp = Vp ? Vp->swap : 0;
     const Pad pd = solver_pad(g.nx, g.ny, g.nz, swp);
+    const OccFrame oc = occ_frame(occ, g, swp);
     __shared__ float s_w[PCAS_KMAX];
     if (threadIdx.x < PCAS_KMAX) {
         float wv = 0.f;                     // static indices keep ws out of local memory
@@ -139,14 +163,21 @@ k_warp_pca(const float* __restrict__ f0h, const T* __restrict__ mean,
             float x[3][4];
             dvf4(mean, U, K, s_w, N, n, x);
             float o[4];
+            int e0 = 4, e1 = -1;                    // first and last non-zero of the four
 #pragma unroll
             for (int e = 0; e < 4; e++) {
-                o[e] = tri_halo(f0h, g, fmaf(x[0][e], g.inv_sx, (float)(i + e)),
-                                 fmaf(x[1][e], g.inv_sy, (float)j), fmaf(x[2][e], g.inv_sz, (float)k));
+                o[e] = tri_halo_m(f0h, occ.f0m, g, fmaf(x[0][e], g.inv_sx, (float)(i + e)),
+                                   fmaf(x[1][e], g.inv_sy, (float)j), fmaf(x[2][e], g.inv_sz, (float)k));
                 if (o[e] != 0.0f) {
                     if (swp) box_add(b, j, i + e, k);
                     else box_add(b, i + e, j, k);
+                    e0 = min(e0, e);
+                    e1 = e;
                 }
+            }
+            if (oc.m && e1 >= 0) {
+                if (swp) occ_mark(oc.m, oc.gen, oc.nbx, oc.nby, j, j, i + e0, i + e1, k);
+                else occ_mark(oc.m, oc.gen, oc.nbx, oc.nby, i + e0, i + e1, j, j, k);
             }
             if (swp) {
 #pragma unroll
@@ -165,15 +196,14 @@ k_warp_pca(const float* __restrict__ f0h, const T* __restrict__ mean,
                 for (int kk = 0; kk < K; kk++) v = fmaf(s_w[kk], ldg_f(U + ((long)kk * 3 + c) * N + n), v);
                 x[c] = v;
             }
-            const float o = tri_halo(f0h, g, fmaf(x[0], g.inv_sx, (float)i), fmaf(x[1], g.inv_sy, (float)j),
-                                      fmaf(x[2], g.inv_sz, (float)k));
-            if (swp) {
-                if (o != 0.0f) box_add(b, j, i, k);
-                fpad[pad_index(pd, j, i, k)] = o;
-            } else {
-                if (o != 0.0f) box_add(b, i, j, k);
-                fpad[pad_index(pd, i, j, k)] = o;
+            const float o = tri_halo_m(f0h, occ.f0m, g, fmaf(x[0], g.inv_sx, (float)i),
+                                        fmaf(x[1], g.inv_sy, (float)j), fmaf(x[2], g.inv_sz, (float)k));
+            const int a0 = swp ? j : i, a1 = swp ? i : j;
+            if (o != 0.0f) {
+                box_add(b, a0, a1, k);
+                if (oc.m) occ_mark(oc.m, oc.gen, oc.nbx, oc.nby, a0, a0, a1, a1, k);
             }
+            fpad[pad_index(pd, a0, a1, k)] = o;
         }
     }
     box_reduce(b, box_out);
@@ -184,15 +214,17 @@ k_warp_pca(const float* __restrict__ f0h, const T* __restrict__ mean,
 // five coefficient vectors; each DVF is formed in the same operation order as
 // the single-volume warp, so a candidate's volume is bit-identical to a lone
 // evaluation.  Output: one float4 (f_0..f_3) per voxel in the candidate
-// buffer and f_4 in the one-volume buffer, zero-halo layout.
+// buffer and f_4 in the one-volume buffer, zero-halo layout; the occupancy
+// bricks mark the union of the five.
 template <typename T, int KT>
-__global__ void __launch_bounds__(kWarpThreads)
+__global__ void __launch_bounds__(kWarpThreads, KT <= 3 ? 6 : (KT <= 5 ? 5 : (KT <= 7 ? 4 : 3)))
 k_warp_batch(const float* __restrict__ f0h, const T* __restrict__ mean,
              const T* __restrict__ U, const SolveState* st, Grid g, const View* __restrict__ Vp,
-             float4* __restrict__ fpad4, float* __restrict__ fpad, int* __restrict__ box_out) {
+             float4* __restrict__ fpad4, float* __restrict__ fpad, int* __restrict__ box_out, Occ occ) {
     if (st->phase >= PH_STOP || st->nvalid < 1) return;    // same gate as the batch projector
     const int swp = Vp ? Vp->swap : 0;
     const Pad pd = solver_pad(g.nx, g.ny, g.nz, swp);
+    const OccFrame oc = occ_frame(occ, g, swp);
     __shared__ float s_w[TRIAL_BATCH][KT];
     if (threadIdx.x < TRIAL_BATCH * KT) {
         const int j = threadIdx.x / KT, k = threadIdx.x % KT;
@@ -231,13 +263,16 @@ k_warp_batch(const float* __restrict__ f0h, const T* __restrict__ mean,
         float o[TRIAL_BATCH];
 #pragma unroll
         for (int b = 0; b < TRIAL_BATCH; b++)
-            o[b] = tri_halo(f0h, g, fmaf(x[b][0], g.inv_sx, (float)i), fmaf(x[b][1], g.inv_sy, (float)j),
-                             fmaf(x[b][2], g.inv_sz, (float)k));
+            o[b] = tri_halo_m(f0h, occ.f0m, g, fmaf(x[b][0], g.inv_sx, (float)i),
+                               fmaf(x[b][1], g.inv_sy, (float)j), fmaf(x[b][2], g.inv_sz, (float)k));
         const int a0 = swp ? j : i, a1 = swp ? i : j;
         const long d = pad_index(pd, a0, a1, k);
         fpad4[d] = make_float4(o[0], o[1], o[2], o[3]);
         fpad[d] = o[4];
-        if (o[0] != 0.0f || o[1] != 0.0f || o[2] != 0.0f || o[3] != 0.0f || o[4] != 0.0f) box_add(bx, a0, a1, k);
+        if (o[0] != 0.0f || o[1] != 0.0f || o[2] != 0.0f || o[3] != 0.0f || o[4] != 0.0f) {
+            box_add(bx, a0, a1, k);
+            if (oc.m) occ_mark(oc.m, oc.gen, oc.nbx, oc.nby, a0, a0, a1, a1, k);
+        }
     }
     box_reduce(bx, box_out);      // every thread of the block, one call site
 }
@@ -276,24 +311,24 @@ cudaError_t pca_dvf_t(const void* mean, const void* U, int K, const float* w, Gr
 
 template <typename T>
 cudaError_t warp_pca_t(const float* f, const void* mean, const void* U, int K, WSrc w, Grid g,
-                       const View* Vd, float* fpad, int* box, cudaStream_t s) {
+                       const View* Vd, float* fpad, int* box, Occ oc, cudaStream_t s) {
     const unsigned a = sizeof(T) * 4;
     bool vec = (g.nx % 4 == 0) && aligned(mean, a) && aligned(U, a) && aligned(fpad, 16);
     const T* m = static_cast<const T*>(mean);
     const T* u = static_cast<const T*>(U);
     const RowLaunch L = row_launch(g, vec ? 4 : 1);
-    if (vec) k_warp_pca<true, T><<<L.grid, L.threads, 0, s>>>(f, m, u, K, w, g, Vd, fpad, box);
-    else k_warp_pca<false, T><<<L.grid, L.threads, 0, s>>>(f, m, u, K, w, g, Vd, fpad, box);
+    if (vec) k_warp_pca<true, T><<<L.grid, L.threads, 0, s>>>(f, m, u, K, w, g, Vd, fpad, box, oc);
+    else k_warp_pca<false, T><<<L.grid, L.threads, 0, s>>>(f, m, u, K, w, g, Vd, fpad, box, oc);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t warp_batch_t(const float* f0, const T* mean, const T* U, int K, const SolveState* st, Grid g,
-                         const View* Vd, float4* fpad4, float* fpad, int* box, const RowLaunch& L,
+                         const View* Vd, float4* fpad4, float* fpad, int* box, Occ oc, const RowLaunch& L,
                          cudaStream_t s) {
     switch (K) {
 #define PCAS_WB_CASE(KK) \
-        case KK: k_warp_batch<T, KK><<<L.grid, L.threads, 0, s>>>(f0, mean, U, st, g, Vd, fpad4, fpad, box); break;
+        case KK: k_warp_batch<T, KK><<<L.grid, L.threads, 0, s>>>(f0, mean, U, st, g, Vd, fpad4, fpad, box, oc); break;
         PCAS_WB_CASE(1) PCAS_WB_CASE(2) PCAS_WB_CASE(3) PCAS_WB_CASE(4)
         PCAS_WB_CASE(5) PCAS_WB_CASE(6) PCAS_WB_CASE(7) PCAS_WB_CASE(8)
 #undef PCAS_WB_CASE
@@ -324,24 +359,24 @@ cudaError_t launch_warp_dvf(const void* f0, int dt, const float* dvf, Grid g, fl
                           cudaGetLastError()))
 }
 
-cudaError_t launch_fill_f0h(const void* f0, int dt, Grid g, float* f0h, cudaStream_t s) {
+cudaError_t launch_fill_f0h(const void* f0, int dt, Grid g, float* f0h, unsigned char* f0m, cudaStream_t s) {
     const RowLaunch L = row_launch(g, 1);
-    PCAS_DT_DISPATCH(dt, (k_fill_f0h<T><<<L.grid, L.threads, 0, s>>>(static_cast<const T*>(f0), g, f0h),
+    PCAS_DT_DISPATCH(dt, (k_fill_f0h<T><<<L.grid, L.threads, 0, s>>>(static_cast<const T*>(f0), g, f0h, f0m),
                           cudaGetLastError()))
 }
 
 cudaError_t launch_warp_pca(const float* f0, const void* mean, const void* U, int dt, int K, WSrc w,
-                            Grid g, const View* Vd, float* fpad, int* box, cudaStream_t s) {
-    PCAS_DT_DISPATCH(dt, (warp_pca_t<T>(f0, mean, U, K, w, g, Vd, fpad, box, s)))
+                            Grid g, const View* Vd, float* fpad, int* box, Occ oc, cudaStream_t s) {
+    PCAS_DT_DISPATCH(dt, (warp_pca_t<T>(f0, mean, U, K, w, g, Vd, fpad, box, oc, s)))
 }
 
 cudaError_t launch_warp_batch(const float* f0, const void* mean, const void* U, int dt, int K,
                               const SolveState* st, Grid g, const View* Vd, float4* fpad4, float* fpad,
-                              cudaStream_t s) {
+                              Occ oc, cudaStream_t s) {
     const RowLaunch L = row_launch(g, 1);
     int* box = const_cast<int*>(st->box[1]);
     PCAS_DT_DISPATCH(dt, (warp_batch_t<T>(f0, static_cast<const T*>(mean),
-                                          static_cast<const T*>(U), K, st, g, Vd, fpad4, fpad, box, L, s)))
+                                          static_cast<const T*>(U), K, st, g, Vd, fpad4, fpad, box, oc, L, s)))
 }
 
 #undef PCAS_DT_DISPATCH

@@ -510,8 +510,10 @@ class Batch:
 class Tuning(C.Structure):
     """pcas_tuning: launch shapes of one size bucket (include/pcasolve.h)."""
     _fields_ = [("ray_lw1", C.c_int), ("chunk1", C.c_int), ("voxel_tile", C.c_int), ("gather_per_sm", C.c_int),
+                ("skip_empty", C.c_int),
                 ("ray_lw4", C.c_ubyte * 8), ("chunk", C.c_ubyte * 8), ("swap", C.c_ubyte * 8)]
-    SCALARS = ("ray_lw1", "chunk1", "voxel_tile", "gather_per_sm")
+    SCALARS = ("ray_lw1", "chunk1", "voxel_tile", "gather_per_sm", "skip_empty")
+    OPTIONAL = {"skip_empty": 1}      # entries written before the field existed
     PER_BIN = ("ray_lw4", "chunk", "swap")
 
     def as_dict(self):
@@ -523,7 +525,7 @@ class Tuning(C.Structure):
 def _tuning_struct(d):
     t = Tuning()
     for k in Tuning.SCALARS:
-        setattr(t, k, int(d[k]))
+        setattr(t, k, int(d[k] if k in d else Tuning.OPTIONAL[k]))
     for k in Tuning.PER_BIN:
         arr = getattr(t, k)
         vals = d[k] if hasattr(d[k], "__len__") else [d[k]] * 8

@@ -63,8 +63,9 @@ def test_workspace_bytes_host_only(lib):
     M = 512 * 384
     cap = 32 * 32 * 25 * 256                                 # 8x8x4 tiles of the Jacobian compaction
     f0h = 262 * 262 * 106 * 4                                # reference CT with a three-voxel zero halo
-    need = f0h + npad * (4 + 16) + M * (6 * 4 + 32) + cap * (4 + 4 * 3)   # f (+ 5th candidate), 4 candidates, 6 projections,
-    assert need <= n < need + 2_000_000 and n % 256 == 0            # ray table, compacted voxels
+    occ = 33 * 33 * 13 * 4                                   # occupancy bricks of 8^3 voxels
+    need = f0h + occ + npad * (4 + 16) + M * (6 * 4 + 32) + cap * (4 + 4 * 3)   # f (+ 5th candidate), 4 candidates,
+    assert need <= n < need + 2_000_000 and n % 256 == 0       # 6 projections, ray table, compacted voxels
     assert P.workspace_bytes(vol, cb, 0) == 0 and P.workspace_bytes(vol, cb, 9) == 0
     # room for the y-fastest layout too: a non-square grid takes the larger of the two
     v2 = S.volume(200, 300, 50, 2.0, 2.0, 2.0)
@@ -161,9 +162,9 @@ def test_tuning_table_host_only(lib):
     cb = S.cone_beam(128, 96, 3.1, 3.1)
     P.tuning_clear()
     d = P.tuning_get(vol, cb, 3)
-    assert d == dict(ray_lw1=3, chunk1=0, voxel_tile=0, gather_per_sm=8, ray_lw4=[3] * 8, chunk=[16] * 8,
-                     swap=[0, 0, 0, 1, 1, 1, 0, 0])
-    t = dict(ray_lw1=2, chunk1=64, voxel_tile=5, gather_per_sm=2, ray_lw4=[2, 3, 4, 2, 3, 4, 2, 3],
+    assert d == dict(ray_lw1=3, chunk1=0, voxel_tile=0, gather_per_sm=8, skip_empty=1, ray_lw4=[3] * 8,
+                     chunk=[16] * 8, swap=[0, 0, 0, 1, 1, 1, 0, 0])
+    t = dict(ray_lw1=2, chunk1=64, voxel_tile=5, gather_per_sm=2, skip_empty=0, ray_lw4=[2, 3, 4, 2, 3, 4, 2, 3],
              chunk=[12, 16, 24, 2, 64, 12, 16, 24], swap=[0, 1] * 4)
     P.tuning_set(vol, cb, 3, t)
     assert P.tuning_get(vol, cb, 3) == t
@@ -172,6 +173,7 @@ def test_tuning_table_host_only(lib):
     assert P.tuning_get(vol, cb, 5) == d and P.tuning_get(vol, cb, 3, dtype=P.BF16) == d
     for bad in (dict(t, ray_lw1=5), dict(t, chunk1=-2), dict(t, chunk1=33), dict(t, chunk1=130),
                 dict(t, voxel_tile=6), dict(t, gather_per_sm=0), dict(t, gather_per_sm=27),
+                dict(t, skip_empty=2), dict(t, skip_empty=-1),
                 dict(t, ray_lw4=[1] + [3] * 7), dict(t, chunk=[13] + [16] * 7), dict(t, chunk=[0] * 8),
                 dict(t, chunk=[66] * 8), dict(t, swap=[2] + [0] * 7)):
         with pytest.raises(P.PcasError):

@@ -32,12 +32,12 @@ def prob():
                         seeds=(71, 72, 73))
 
 
-SHAPES = [dict(ray_lw1=2, chunk1=0, voxel_tile=1, gather_per_sm=4, ray_lw4=[4] * 8, chunk=[12] * 8),
-          dict(ray_lw1=4, chunk1=32, voxel_tile=2, gather_per_sm=16, ray_lw4=[2] * 8, chunk=[24] * 8),
-          dict(ray_lw1=3, chunk1=64, voxel_tile=3, gather_per_sm=1, ray_lw4=[3] * 8, chunk=[16] * 8),
-          dict(ray_lw1=2, chunk1=2, voxel_tile=4, gather_per_sm=26, ray_lw4=[2] * 8, chunk=[2] * 8),
-          dict(ray_lw1=4, chunk1=128, voxel_tile=5, gather_per_sm=8, ray_lw4=[4] * 8, chunk=[64] * 8),
-          dict(ray_lw1=3, chunk1=0, voxel_tile=0, gather_per_sm=8, ray_lw4=[2, 3, 4, 2, 3, 4, 2, 3],
+SHAPES = [dict(ray_lw1=2, chunk1=0, voxel_tile=1, gather_per_sm=4, skip_empty=1, ray_lw4=[4] * 8, chunk=[12] * 8),
+          dict(ray_lw1=4, chunk1=32, voxel_tile=2, gather_per_sm=16, skip_empty=0, ray_lw4=[2] * 8, chunk=[24] * 8),
+          dict(ray_lw1=3, chunk1=64, voxel_tile=3, gather_per_sm=1, skip_empty=1, ray_lw4=[3] * 8, chunk=[16] * 8),
+          dict(ray_lw1=2, chunk1=2, voxel_tile=4, gather_per_sm=26, skip_empty=1, ray_lw4=[2] * 8, chunk=[2] * 8),
+          dict(ray_lw1=4, chunk1=128, voxel_tile=5, gather_per_sm=8, skip_empty=0, ray_lw4=[4] * 8, chunk=[64] * 8),
+          dict(ray_lw1=3, chunk1=0, voxel_tile=0, gather_per_sm=8, skip_empty=1, ray_lw4=[2, 3, 4, 2, 3, 4, 2, 3],
                chunk=[12, 24, 16, 2, 64, 12, 16, 24])]
 
 
@@ -70,15 +70,15 @@ def test_autotune_stores_a_valid_entry(P, prob):
     d = to_dev(pb)
     P.tuning_clear()
     default = P.tuning_get(pb["vol"], pb["cb"], 3)
-    assert default == dict(ray_lw1=3, chunk1=0, voxel_tile=0, gather_per_sm=8, ray_lw4=[3] * 8, chunk=[16] * 8,
-                           swap=[0, 0, 0, 1, 1, 1, 0, 0])
+    assert default == dict(ray_lw1=3, chunk1=0, voxel_tile=0, gather_per_sm=8, skip_empty=1, ray_lw4=[3] * 8,
+                           chunk=[16] * 8, swap=[0, 0, 0, 1, 1, 1, 0, 0])
     prm = P.default_params(pb["step"])
     t = P.autotune(d["f0"], None, d["U"], d["y"], pb["vol"], pb["cb"], prm)
     print("autotuned:", t)
     assert t == P.tuning_get(pb["vol"], pb["cb"], 3)
     assert 2 <= t["ray_lw1"] <= 4 and t["chunk1"] in (0, 32, 64)
     assert all(2 <= v <= 4 for v in t["ray_lw4"]) and all(v in (12, 16, 24) for v in t["chunk"])
-    assert 0 <= t["voxel_tile"] < 6 and t["gather_per_sm"] in (4, 8, 16)
+    assert 0 <= t["voxel_tile"] < 6 and t["gather_per_sm"] in (4, 8, 16) and t["skip_empty"] in (0, 1)
     # the tuned table drives both solve paths identically, within parity of the oracle
     wh, sth = P.solve_projection(d["f0"], None, d["U"], d["y"], pb["vol"], pb["cb"], np.zeros(3), prm)
     sv = P.Solver(d["f0"], None, d["U"], pb["vol"], pb["cb"], prm)
