@@ -189,6 +189,10 @@ class ClockSampler:
 
 
 # --------------------------------------------------------- algorithmic bytes
+# size of the per-projection result record a queued solve copies back
+SEQ_OUT_BYTES = 8 * 8 + 4 * 8 + 5 * 8 + 4 * 4
+
+
 def kernel_bytes(N, M, K, has_mean):
     """Algorithmic HBM bytes per launch of each solver kernel (float32)."""
     model = 12 * K * N + (12 * N if has_mean else 0)
@@ -305,8 +309,9 @@ def run_ours(args, ws_, rank, local):
         P.tuning_clear()
     solver = P.Solver(tf0, None, tU, vol, view(0.0), prm, device=dev)
 
-    def solve_range(t0, t1, hist, y_of, stats_out, mode="graph"):
-        """Sequence driver: Eq. (3) warm start, solve, localise, per projection."""
+    def solve_range(t0, t1, hist, y_of, stats_out):
+        """Host-driven sequence driver (every kernel launched and timed from the
+        host): Eq. (3) warm start, solve, localise, per projection."""
         for t in range(t0, t1):
             if t == 0:
                 w0 = np.zeros(K)
@@ -314,36 +319,36 @@ def run_ours(args, ws_, rank, local):
                 w0 = hist[-1]
             else:
                 w0 = P.lp_predict(np.stack([hist[-1], hist[-2]]), c_lp)
-            if mode == "graph":                 # device-driven solve: one graph launch
-                w, st = solver.solve(y_of(t), w0, angle=angles[t])
-            else:                               # host-driven loop, kernels individually timed
-                w, st = P.solve_projection(tf0, None, tU, y_of(t), vol, view(angles[t]), w0, prm, ws=wsp)
+            w, st = P.solve_projection(tf0, None, tU, y_of(t), vol, view(angles[t]), w0, prm, ws=wsp)
             c, _ = P.localize_tumor(None, tU, w, vol, c_ref)
             hist.append(w)
             stats_out.append((t, st, c))
 
-    # warm-up projections (also builds the prediction history)
-    hist, warm = [], []
-    solve_range(0, W_, hist, lambda t: ys[t], warm)
-    solve_range(0, 2, [], lambda t: ys[t], [], mode="host")
+    # warm-up projections: the start of a run of the device-driven solver (the
+    # Eq. 3 warm start and the localisation inside its graph), which the timed
+    # projections continue; also builds the host-side history
+    stream = torch.cuda.current_stream()
+    solver.seq_begin(c_lp, c_ref)
+    warm = solver.solve_sequence([ys[t] for t in range(W_)], angles[:W_], w_first=np.zeros(K))
+    hist = [w for w, _, _, _ in warm]
+    solve_range(0, 2, [], lambda t: ys[t], [])
     torch.cuda.synchronize()
 
-    # ---- timed region: inputs resident in HBM, device-driven solves
-    stream = torch.cuda.current_stream()
+    # ---- timed region: inputs resident in HBM, device-driven solves queued back to back
     P.profile(False)
-    timed = []
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         if ws_ > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
         ev0.record(stream)
-        solve_range(W_, n_used, hist, lambda t: ys[t], timed)
+        res = solver.solve_sequence([ys[t] for t in range(W_, n_used)], angles[W_:n_used])
         ev1.record(stream)
         torch.cuda.synchronize()
         if ws_ > 1:
             torch.distributed.barrier()
     ms = ev0.elapsed_time(ev1)
+    timed = [(W_ + i, st, c) for i, (w, st, c, _) in enumerate(res)]
     launches_timed = sum(n for n, _ in P.profile_read().values())
     clocks = clk.summary()
 
@@ -353,29 +358,23 @@ def run_ours(args, ws_, rank, local):
     h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     h0.record(stream)
-    solve_range(W_, n_used, list(hist[:W_]), lambda t: ys[t], timed_host, mode="host")
+    solve_range(W_, n_used, list(hist[:W_]), lambda t: ys[t], timed_host)
     h1.record(stream)
     torch.cuda.synchronize()
     ms_host = h0.elapsed_time(h1)
     prof = P.profile_read()
     P.profile(False)
 
-    # ---- end to end: per step, y from pinned host memory, result back to host
+    # ---- end to end: per step, y copied from pinned host memory inside the
+    # queued solve and its result record read back to pinned host memory
     y_host = ys.cpu().pin_memory()
-    y_dev = torch.empty(M, dtype=torch.float32, device=dev)
-    hist_e2e = list(hist[:W_])
-    e2e_stats = []
-
-    def y_e2e(t):
-        y_dev.copy_(y_host[t], non_blocking=True)
-        return y_dev
-
+    solver.seq_begin(c_lp, c_ref, w_hist=[hist[W_ - 1], hist[W_ - 2]])
     if ws_ > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    solve_range(W_, n_used, hist_e2e, y_e2e, e2e_stats)
+    res_e2e = solver.solve_sequence([y_host[t] for t in range(W_, n_used)], angles[W_:n_used])
     e1.record(stream)
     torch.cuda.synchronize()
     ms_e2e = e0.elapsed_time(e1)
@@ -446,8 +445,8 @@ def run_ours(args, ws_, rank, local):
         "solver": {"iters_mean": round(float(iters.mean()), 3), "evals_mean": round(float(evals.mean()), 3)},
         "e2e": {"value": round(replica_throughput(ws_, K_, te_s), 3), "unit": "projections/s",
                 "h2d_bytes_per_step": 4 * M,
-                # solver state read back once per solve (1040 B), 32 B of centroid
-                "d2h_bytes_per_step": 1072},
+                # the projection's result record (solution, centroid, statistics)
+                "d2h_bytes_per_step": SEQ_OUT_BYTES},
     }
     if ws_ == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(vol, f0, c_ref, U, trace, train, angles, ys, W_)

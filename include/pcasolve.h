@@ -228,6 +228,40 @@ float* pcas_solver_y_buffer(pcas_solver solver);
 int pcas_solver_solve(pcas_solver solver, const float* y, double angle_rad, double off_u, double off_v,
                       const double* w_init, double* w_out, pcas_stats* stats, void* stream);
 int pcas_solver_destroy(pcas_solver solver);
+
+/* Runs of consecutive projections on one solver (a breathing sequence): the
+ * warm start of Eq. (3) and the tumour localisation of Sec. II.A run inside
+ * the graph, from the solutions the run keeps on the device, so projections
+ * can be queued back to back with no host round trip in between.
+ * pcas_solver_seq_begin: starts a run.  lp_coef: host K x L (c[k][l] as
+ *   lp_fit, 1 <= L <= 8); c_ref: tumour centroid in the reference CT (mm);
+ *   loc_max_iter, loc_tol_mm: as localize_tumor; w_hist: host n_hist x K
+ *   solutions preceding the run, latest first (0 <= n_hist <= 8; NULL when
+ *   0).  Synchronous.
+ * pcas_solver_seq_enqueue: queues one projection on the stream and returns
+ *   its ticket.  y: [nv][nu] floats, device or (pinned) host memory, copied
+ *   into the solver's buffer; the view is the creation view at angle_rad.
+ *   The start is w_first (host, K doubles, NULL = zeros) while the run has
+ *   no solution yet, then the latest solution while it has fewer than L,
+ *   then the Eq. (3) prediction from the last L (the same arithmetic as
+ *   lp_predict).  Returns before the solve runs; at most 64 projections of a
+ *   solver may be in flight (the call waits for a free slot).
+ * pcas_solver_seq_result: waits for the projection of a ticket and returns
+ *   its solution, centroid and statistics (host); valid for the last 64
+ *   tickets of the solver.  Returns PCAS_ERR_SINGULAR for a constant image
+ *   (the run goes on from the unchanged start).
+ * A pcas_solver_solve or batch solve in between ends the run. */
+typedef struct {
+    double w[PCAS_KMAX];      /* solution (first K entries) */
+    double c[3];              /* tumour centroid, mm */
+    int loc_converged;        /* 1 if the localisation converged */
+    pcas_stats stats;
+} pcas_seq_result;
+int pcas_solver_seq_begin(pcas_solver solver, const double* lp_coef, int L, const double* c_ref,
+                          int loc_max_iter, double loc_tol_mm, const double* w_hist, int n_hist, void* stream);
+int pcas_solver_seq_enqueue(pcas_solver solver, const void* y, double angle_rad, const double* w_first,
+                            long long* ticket, void* stream);
+int pcas_solver_seq_result(pcas_solver solver, long long ticket, pcas_seq_result* out);
 int pcas_batch_create(pcas_batch* out, const pcas_solver* solvers, const float* const* y_src, int n,
                       void* stream);
 int pcas_batch_solve(pcas_batch batch, const double* angle_rad, const double* w_init, double* w_out,

@@ -344,14 +344,14 @@ int gather_blocks(const Tune& T) {
 }
 
 // ------------------------------------------------------------ small kernels
+// Sec. II.A fixed point c = c_ref - x(c) for the tumour centroid, by one warp:
+// lanes 0..7 own the eight taps of the trilinear DVF sample (Eq. 1 at w).
+// Lane 0 writes out[0..2] = c and out[3] = 1 if it converged (else 0).
 template <typename T>
-__global__ void k_localize(const T* __restrict__ mean, const T* __restrict__ U, int K,
-                           Grid g, double w0, double w1, double w2, double w3, double w4, double w5,
-                           double w6, double w7, double ox, double oy, double oz, double isx,
-                           double isy, double isz, double cx, double cy, double cz, int max_iter,
-                           double tol, double* out) {
-    // one warp: lanes 0..7 own the eight taps of the trilinear DVF sample
-    const double w[PCAS_KMAX] = {w0, w1, w2, w3, w4, w5, w6, w7};
+__device__ void localize_warp(const T* __restrict__ mean, const T* __restrict__ U, int K, const Grid& g,
+                              const double* w, double ox, double oy, double oz, double isx, double isy,
+                              double isz, double cx, double cy, double cz, int max_iter, double tol,
+                              double* out) {
     const int lane = threadIdx.x;
     const long N = (long)g.nx * g.ny * g.nz;
     double y[3] = {0.0, 0.0, 0.0};
@@ -398,6 +398,16 @@ __global__ void k_localize(const T* __restrict__ mean, const T* __restrict__ U, 
         out[2] = cz + y[2];
         out[3] = converged ? 1.0 : 0.0;
     }
+}
+
+template <typename T>
+__global__ void k_localize(const T* __restrict__ mean, const T* __restrict__ U, int K,
+                           Grid g, double w0, double w1, double w2, double w3, double w4, double w5,
+                           double w6, double w7, double ox, double oy, double oz, double isx,
+                           double isy, double isz, double cx, double cy, double cz, int max_iter,
+                           double tol, double* out) {
+    const double w[PCAS_KMAX] = {w0, w1, w2, w3, w4, w5, w6, w7};
+    localize_warp(mean, U, K, g, w, ox, oy, oz, isx, isy, isz, cx, cy, cz, max_iter, tol, out);
 }
 
 // Reset the solver state for a new evaluation/solve.
@@ -1226,9 +1236,9 @@ int lp_fit(const double* trace, int T, int K, int L, double* c) {
 int lp_predict(const double* hist, const double* c, int K, int L, double* w0) {
     if (!hist || !c || !w0) return fail(PCAS_ERR_INVALID_ARG, "hist, c and w0 must be non-NULL");
     if (K < 1 || L < 1) return fail(PCAS_ERR_INVALID_ARG, "need K >= 1 and L >= 1");
-    for (int k = 0; k < K; k++) {
+    for (int k = 0; k < K; k++) {          // fused multiply-adds in l order (as the device warm start)
         double acc = 0.0;
-        for (int l = 0; l < L; l++) acc += c[k * L + l] * hist[(long)l * K + k];
+        for (int l = 0; l < L; l++) acc = fma(c[k * L + l], hist[(long)l * K + k], acc);
         w0[k] = acc;
     }
     return PCAS_OK;
@@ -1245,22 +1255,66 @@ int lp_predict(const double* hist, const double* c, int K, int L, double* w0) {
 // of these sets its condition on every path out.  Both loops are bounded by construction:
 // an iteration either accepts a step (at most max_iter of them) or ends the
 // solve, and every batch tries at least one step size of the iteration's
-// schedule (at most max_trials).  The view and the initial coefficients come
-// from pinned host buffers through memcpy nodes, so one instantiated graph
-// serves every gantry angle.
+// schedule (at most max_trials).  The view and the initial coefficients are
+// copied in before each launch from a ring of pinned host slots, so one
+// instantiated graph serves every gantry angle, and launches can be queued
+// ahead.  In a run of consecutive projections (pcas_solver_seq_*) the warm
+// start of Eq. (3) is taken on the device from the solutions kept there, and
+// the graph ends with the tumour localisation of Sec. II.A: projection after
+// projection goes by without a host round trip.
 // ===========================================================================
 namespace {
 
 struct InitBlock {
     double w[PCAS_KMAX];
     double mu0, alpha, beta, mu_min;
-    int K, max_trials, max_iter, pad;
+    int K, max_trials, max_iter;
+    int seq;                  // 1: start from the run's history (Eq. 3), localise at the end
 };
 
-__global__ void k_init_dev(SolveState* st, const InitBlock* __restrict__ ib) {
+// Per-launch staging (view + start), one device copy and SEQ_RING host slots.
+struct Stage {
+    View v;
+    InitBlock ib;
+};
+
+enum { LP_MAX = 8, SEQ_RING = 64 };
+
+// A run of consecutive projections: the Eq. (3) predictor, the localisation
+// parameters, and the solutions so far (hist[0] the latest).
+struct SeqBlock {
+    double lp[PCAS_KMAX * LP_MAX];    // c[k * L + l] as lp_fit
+    double c_ref[3], loc_tol;
+    double o[3], is[3];               // volume origin and reciprocal spacing
+    int L, loc_max_iter;
+    int n, pad;                       // solutions in the history (n >= L: full predictor)
+    double hist[LP_MAX][PCAS_KMAX];
+};
+
+// Result of one projection of a run, copied to a host slot after the launch.
+struct SeqOut {
+    double w[PCAS_KMAX];
+    double c[4];                      // centroid (mm) and 1 if the fixed point converged
+    double J0, J, a, b, mu;
+    int iters, evals, phase, launches;
+};
+
+// Eq. (3) on the device: w0 = sum_l c[k][l] w*(t-1-l) with fused
+// multiply-adds in l order, exactly as the host lp_predict.  Before L
+// solutions exist the run starts from the latest one (or from ib->w first).
+__device__ double seq_start(const SeqBlock* sq, const InitBlock* ib, int k) {
+    const int n = sq->n, L = sq->L;
+    if (n == 0) return ib->w[k];
+    if (n < L) return sq->hist[0][k];
+    double acc = 0.0;
+    for (int l = 0; l < L; l++) acc = fma(sq->lp[k * L + l], sq->hist[l][k], acc);
+    return acc;
+}
+
+__global__ void k_init_dev(SolveState* st, const InitBlock* __restrict__ ib, const SeqBlock* __restrict__ sq) {
     if (threadIdx.x != 0) return;
     for (int k = 0; k < PCAS_KMAX; k++) {
-        st->w[k] = k < ib->K ? ib->w[k] : 0.0;
+        st->w[k] = k < ib->K ? (ib->seq ? seq_start(sq, ib, k) : ib->w[k]) : 0.0;
         st->d[k] = 0.0;
         st->G[k] = 0.0;
         for (int j = 0; j < TRIAL_BATCH; j++) st->wt[j][k] = st->w[k];
@@ -1297,6 +1351,33 @@ __global__ void k_ctrl_iter_end(SolveState* st, cudaGraphConditionalHandle h_out
     if (ph == PH_ACCEPT || ph == PH_STOP) st->iters += 1;
     const bool more = ph == PH_ACCEPT && st->iters < st->max_iter;
     cudaGraphSetConditional(h_outer, more ? 1u : 0u);
+}
+
+// End of a device-driven solve (one warp).  In a run: the tumour centroid at
+// the solution (Sec. II.A, the same fixed point as localize_tumor), the
+// solution pushed onto the history, and the result record.
+template <typename T>
+__global__ void k_seq_end(SolveState* st, const InitBlock* __restrict__ ib, SeqBlock* sq, SeqOut* out,
+                          const T* __restrict__ mean, const T* __restrict__ U, int K, Grid g) {
+    if (!ib->seq) {
+        if (threadIdx.x == 0) st->launches += 1;
+        return;
+    }
+    double w[PCAS_KMAX];
+    for (int k = 0; k < PCAS_KMAX; k++) w[k] = st->w[k];
+    double c[4];
+    localize_warp(mean, U, K, g, w, sq->o[0], sq->o[1], sq->o[2], sq->is[0], sq->is[1], sq->is[2],
+                  sq->c_ref[0], sq->c_ref[1], sq->c_ref[2], sq->loc_max_iter, sq->loc_tol, c);
+    if (threadIdx.x != 0) return;
+    for (int l = LP_MAX - 1; l > 0; l--)
+        for (int k = 0; k < PCAS_KMAX; k++) sq->hist[l][k] = sq->hist[l - 1][k];
+    for (int k = 0; k < PCAS_KMAX; k++) sq->hist[0][k] = w[k];
+    if (sq->n < LP_MAX) sq->n += 1;
+    st->launches += 1;
+    for (int k = 0; k < PCAS_KMAX; k++) out->w[k] = w[k];
+    for (int i = 0; i < 4; i++) out->c[i] = c[i];
+    out->J0 = st->J0; out->J = st->J; out->a = st->a; out->b = st->b; out->mu = st->mu;
+    out->iters = st->iters; out->evals = st->evals; out->phase = st->phase; out->launches = st->launches;
 }
 
 #define PCAS_G(call)                                                                              \
@@ -1339,9 +1420,17 @@ struct pcas_solver_s {
     const void *f0, *mean, *U;
     Ws W;
     float* y;             // device, M floats (in the workspace)
-    InitBlock* d_init;    // device (in the workspace)
-    View* h_view;         // pinned host staging
-    InitBlock* h_init;
+    Stage* d_stage;       // device (in the workspace): view + start of the next launch
+    SeqBlock* d_seq;      // device: the run of consecutive projections
+    SeqOut* d_out;        // device: result of the last projection of a run
+    Stage* h_ring;        // pinned host [SEQ_RING]: staging per launch
+    SeqOut* h_out;        // pinned host [SEQ_RING]: results of a run
+    SeqBlock* h_seq;      // pinned host: run parameters on their way to the device
+    cudaEvent_t ev[SEQ_RING];   // a slot is free again once its launch passed this
+    long long next;       // tickets handed out (slot = ticket % SEQ_RING)
+    long long seq_first;  // first ticket of the current run (-1: no run)
+    long long slot_ticket[SEQ_RING];  // ticket of a run's projection in each slot (-1: none)
+    bool slot_counted[SEQ_RING];      // its launches already added to the profile
     SolveState* h_state;
     cudaGraphConditionalHandle h_outer, h_inner;
     cudaGraph_t graph;
@@ -1360,7 +1449,8 @@ struct pcas_batch_s {
 namespace {
 
 size_t solver_extra(const pcas_cb* cb) {
-    return align256((size_t)cb->nu * cb->nv * sizeof(float)) + align256(sizeof(InitBlock));
+    return align256((size_t)cb->nu * cb->nv * sizeof(float)) + align256(sizeof(Stage)) + align256(sizeof(SeqBlock)) +
+           align256(sizeof(SeqOut));
 }
 
 // Captures one device-driven solve into `graph` as an independent branch
@@ -1396,9 +1486,7 @@ int capture_solve(pcas_solver s, cudaGraph_t graph, cudaStream_t cs, const float
     // prologue
     PCAS_G(cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     if (y_src) PCAS_G(cudaMemcpyAsync(s->y, y_src, M * sizeof(float), cudaMemcpyDeviceToDevice, cs));
-    PCAS_G(cudaMemcpyAsync(W.view, s->h_view, sizeof(View), cudaMemcpyHostToDevice, cs));
-    PCAS_G(cudaMemcpyAsync(s->d_init, s->h_init, sizeof(InitBlock), cudaMemcpyHostToDevice, cs));
-    k_init_dev<<<1, 32, 0, cs>>>(W.st, s->d_init);
+    k_init_dev<<<1, 32, 0, cs>>>(W.st, &s->d_stage->ib, s->d_seq);
     PCAS_G(cudaGetLastError());
     const Occ oc = occ_of(W, s->tune);
     PCAS_G(launch_fill_f0h(s->f0, s->dtype, g, W.f0h, s->tune.skip ? W.f0m : nullptr, cs));  // f0 may change
@@ -1412,6 +1500,24 @@ int capture_solve(pcas_solver s, cudaGraph_t graph, cudaStream_t cs, const float
     PCAS_G(cudaGetLastError());
     cudaGraph_t outer_body;
     PCAS_TRY(add_while(cs, s->h_outer, &outer_body));
+    switch (s->dtype) {
+        case DT_F32:
+            k_seq_end<float><<<1, 32, 0, cs>>>(W.st, &s->d_stage->ib, s->d_seq, s->d_out,
+                                               static_cast<const float*>(s->mean),
+                                               static_cast<const float*>(s->U), s->K, g);
+            break;
+        case DT_BF16:
+            k_seq_end<__nv_bfloat16><<<1, 32, 0, cs>>>(W.st, &s->d_stage->ib, s->d_seq, s->d_out,
+                                                       static_cast<const __nv_bfloat16*>(s->mean),
+                                                       static_cast<const __nv_bfloat16*>(s->U), s->K, g);
+            break;
+        default:
+            k_seq_end<__half><<<1, 32, 0, cs>>>(W.st, &s->d_stage->ib, s->d_seq, s->d_out,
+                                                static_cast<const __half*>(s->mean),
+                                                static_cast<const __half*>(s->U), s->K, g);
+            break;
+    }
+    PCAS_G(cudaGetLastError());
     cudaGraph_t done;
     PCAS_G(cudaStreamEndCapture(cs, &done));
     // one iteration: residual + gradient, then the candidate batches
@@ -1441,26 +1547,48 @@ int capture_solve(pcas_solver s, cudaGraph_t graph, cudaStream_t cs, const float
 
 #undef PCAS_G
 
-int solver_stage(pcas_solver s, double angle_rad, double off_u, double off_v, const double* w_init,
-                 cudaStream_t st) {
+// Takes the next staging slot (waiting until the launch that last used it
+// has passed it) and returns its index; the ticket is s->next - 1.
+int solver_slot(pcas_solver s, int* slot) {
+    const int i = (int)(s->next % SEQ_RING);
+    if (s->next >= SEQ_RING) PCAS_CUDA(cudaEventSynchronize(s->ev[i]));
+    s->slot_ticket[i] = -1;               // its previous result, if any, is gone
+    s->next += 1;
+    *slot = i;
+    return PCAS_OK;
+}
+
+// Stages the view of this angle and the start of a solve in a ring slot and
+// enqueues its copy to the device (plus the zeroing of the solver volumes
+// when the layout changes).  seq: start from the run's history instead of
+// w_init (which is then only used for the run's first projection, may be NULL).
+int solver_stage(pcas_solver s, double angle_rad, double off_u, double off_v, const double* w_init, int seq,
+                 int* slot_out, cudaStream_t st) {
     pcas_cb cb = s->cb;
     cb.angle_rad = angle_rad;
     cb.off_u = off_u;
     cb.off_v = off_v;
     View V;
     PCAS_TRY(make_view(&s->vol, &cb, s->prm.step_mm, &V));
-    PCAS_TRY(check_finite(w_init, s->K, "w_init"));
+    if (w_init) PCAS_TRY(check_finite(w_init, s->K, "w_init"));
+    else if (!seq) return fail(PCAS_ERR_INVALID_ARG, "w_init is NULL");
     set_layouts(V, s->tune, angle_rad);
+    int slot;
+    PCAS_TRY(solver_slot(s, &slot));
     const int lay = V.swap;
     if (s->layout >= 0 && s->layout != lay)   // the other layout's voxels lie on this one's halo
         PCAS_CUDA(cudaMemsetAsync(s->W.fpad, 0, s->W.fpad_bytes + s->W.fpad4_bytes, st));
     s->layout = lay;
-    *s->h_view = V;
+    Stage& h = s->h_ring[slot];
+    h.v = V;
     InitBlock ib = {};
-    for (int k = 0; k < s->K; k++) ib.w[k] = w_init[k];
+    for (int k = 0; k < s->K; k++) ib.w[k] = w_init ? w_init[k] : 0.0;
     ib.mu0 = s->prm.mu0; ib.alpha = s->prm.alpha; ib.beta = s->prm.beta; ib.mu_min = s->prm.mu_min;
     ib.K = s->K; ib.max_trials = s->prm.max_trials; ib.max_iter = s->prm.max_iter;
-    *s->h_init = ib;
+    ib.seq = seq;
+    h.ib = ib;
+    PCAS_CUDA(cudaMemcpyAsync(s->d_stage, &h, sizeof(Stage), cudaMemcpyHostToDevice, st));
+    if (slot_out) *slot_out = slot;
     return PCAS_OK;
 }
 
@@ -1486,8 +1614,11 @@ void solver_free(pcas_solver s) {
     if (!s) return;
     if (s->exec) cudaGraphExecDestroy(s->exec);
     if (s->graph) cudaGraphDestroy(s->graph);
-    if (s->h_view) cudaFreeHost(s->h_view);
-    if (s->h_init) cudaFreeHost(s->h_init);
+    for (int i = 0; i < SEQ_RING; i++)
+        if (s->ev[i]) cudaEventDestroy(s->ev[i]);
+    if (s->h_ring) cudaFreeHost(s->h_ring);
+    if (s->h_out) cudaFreeHost(s->h_out);
+    if (s->h_seq) cudaFreeHost(s->h_seq);
     if (s->h_state) cudaFreeHost(s->h_state);
     delete s;
 }
@@ -1528,14 +1659,25 @@ int pcas_solver_create(pcas_solver* out, const void* f0, const void* mean, const
     int rc = bind_ws(ws, base, vol, cb, K, &s->W);
     if (rc != PCAS_OK) { solver_free(s); return rc; }
     char* extra = static_cast<char*>(ws) + base;
+    size_t off = align256((size_t)cb->nu * cb->nv * sizeof(float));
     s->y = reinterpret_cast<float*>(extra);
-    s->d_init = reinterpret_cast<InitBlock*>(extra + align256((size_t)cb->nu * cb->nv * sizeof(float)));
+    s->d_stage = reinterpret_cast<Stage*>(extra + off);
+    off += align256(sizeof(Stage));
+    s->d_seq = reinterpret_cast<SeqBlock*>(extra + off);
+    off += align256(sizeof(SeqBlock));
+    s->d_out = reinterpret_cast<SeqOut*>(extra + off);
+    s->W.view = &s->d_stage->v;           // the kernels read the staged view
+    s->seq_first = -1;
+    for (int i = 0; i < SEQ_RING; i++) s->slot_ticket[i] = -1;
     cudaStream_t st = as_stream(stream);
     cudaStream_t cs = nullptr;
     cudaError_t e = cudaGetDevice(&s->device);
-    if (e == cudaSuccess) e = cudaHostAlloc((void**)&s->h_view, sizeof(View), cudaHostAllocDefault);
-    if (e == cudaSuccess) e = cudaHostAlloc((void**)&s->h_init, sizeof(InitBlock), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&s->h_ring, SEQ_RING * sizeof(Stage), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&s->h_out, SEQ_RING * sizeof(SeqOut), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&s->h_seq, sizeof(SeqBlock), cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&s->h_state, sizeof(SolveState), cudaHostAllocDefault);
+    for (int i = 0; i < SEQ_RING && e == cudaSuccess; i++)
+        e = cudaEventCreateWithFlags(&s->ev[i], cudaEventDisableTiming);
     // zero the halos once: the warp kernels never write them
     if (e == cudaSuccess) e = cudaMemsetAsync(s->W.fpad, 0, s->W.fpad_bytes + s->W.fpad4_bytes, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->W.f0h, 0, s->W.f0h_bytes, st);
@@ -1547,7 +1689,6 @@ int pcas_solver_create(pcas_solver* out, const void* f0, const void* mean, const
         solver_free(s);
         return fail(PCAS_ERR_CUDA, "solver set-up failed: %s", cudaGetErrorString(e));
     }
-    *s->h_view = s->view0;
     rc = capture_solve(s, s->graph, cs, nullptr);
     cudaStreamDestroy(cs);
     if (rc != PCAS_OK) { solver_free(s); return rc; }
@@ -1567,17 +1708,101 @@ int pcas_solver_solve(pcas_solver s, const float* y, double angle_rad, double of
     PCAS_TRY(check_ptr(s, "solver"));
     PCAS_TRY(check_ptr(w_init, "w_init"));
     cudaStream_t st = as_stream(stream);
-    PCAS_TRY(solver_stage(s, angle_rad, off_u, off_v, w_init, st));
+    int slot;
+    PCAS_TRY(solver_stage(s, angle_rad, off_u, off_v, w_init, 0, &slot, st));
     const size_t M = (size_t)s->cb.nu * s->cb.nv;
     if (y && y != s->y) PCAS_CUDA(cudaMemcpyAsync(s->y, y, M * sizeof(float), cudaMemcpyDeviceToDevice, st));
     PCAS_CUDA(cudaGraphLaunch(s->exec, st));
     PCAS_CUDA(cudaMemcpyAsync(s->h_state, s->W.st, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
+    PCAS_CUDA(cudaEventRecord(s->ev[slot], st));
     PCAS_CUDA(cudaStreamSynchronize(st));
+    s->seq_first = -1;                    // a solve in between ends a run
     {
         std::lock_guard<std::mutex> lk(g_prof_mutex);
         g_launches[PCAS_K_GRAPH] += s->h_state->launches;
     }
     return solver_collect(s, w_out, stats);
+}
+
+int pcas_solver_seq_begin(pcas_solver s, const double* lp_coef, int L, const double* c_ref, int loc_max_iter,
+                          double loc_tol_mm, const double* w_hist, int n_hist, void* stream) {
+    PCAS_TRY(check_ptr(s, "solver"));
+    PCAS_TRY(check_ptr(lp_coef, "lp_coef"));
+    PCAS_TRY(check_ptr(c_ref, "c_ref"));
+    if (L < 1 || L > LP_MAX) return fail(PCAS_ERR_INVALID_ARG, "predictor order L must be in [1, %d]", (int)LP_MAX);
+    if (n_hist < 0 || n_hist > LP_MAX || (n_hist > 0 && !w_hist))
+        return fail(PCAS_ERR_INVALID_ARG, "n_hist must be in [0, %d] (w_hist non-NULL when > 0)", (int)LP_MAX);
+    if (loc_max_iter < 1 || loc_max_iter > 100000 || !(loc_tol_mm > 0))
+        return fail(PCAS_ERR_INVALID_ARG, "loc_max_iter must be in [1, 1e5] and loc_tol_mm > 0");
+    PCAS_TRY(check_finite(lp_coef, s->K * L, "lp_coef"));
+    PCAS_TRY(check_finite(c_ref, 3, "c_ref"));
+    if (n_hist > 0) PCAS_TRY(check_finite(w_hist, s->K * n_hist, "w_hist"));
+    cudaStream_t st = as_stream(stream);
+    PCAS_CUDA(cudaStreamSynchronize(st));           // the previous run's copy of h_seq is done
+    SeqBlock& h = *s->h_seq;
+    memset(&h, 0, sizeof(SeqBlock));
+    for (int k = 0; k < s->K; k++)
+        for (int l = 0; l < L; l++) h.lp[k * L + l] = lp_coef[k * L + l];
+    for (int c = 0; c < 3; c++) h.c_ref[c] = c_ref[c];
+    h.loc_tol = loc_tol_mm;
+    h.loc_max_iter = loc_max_iter;
+    h.o[0] = s->vol.ox; h.o[1] = s->vol.oy; h.o[2] = s->vol.oz;
+    h.is[0] = 1.0 / s->vol.sx; h.is[1] = 1.0 / s->vol.sy; h.is[2] = 1.0 / s->vol.sz;
+    h.L = L;
+    h.n = n_hist;
+    for (int l = 0; l < n_hist; l++)
+        for (int k = 0; k < s->K; k++) h.hist[l][k] = w_hist[(size_t)l * s->K + k];
+    PCAS_CUDA(cudaMemcpyAsync(s->d_seq, s->h_seq, sizeof(SeqBlock), cudaMemcpyHostToDevice, st));
+    PCAS_CUDA(cudaStreamSynchronize(st));
+    s->seq_first = s->next;
+    return PCAS_OK;
+}
+
+int pcas_solver_seq_enqueue(pcas_solver s, const void* y, double angle_rad, const double* w_first,
+                            long long* ticket, void* stream) {
+    PCAS_TRY(check_ptr(s, "solver"));
+    PCAS_TRY(check_ptr(ticket, "ticket"));
+    if (s->seq_first < 0) return fail(PCAS_ERR_INVALID_ARG, "no run of projections: call pcas_solver_seq_begin");
+    cudaStream_t st = as_stream(stream);
+    int slot;
+    PCAS_TRY(solver_stage(s, angle_rad, s->cb.off_u, s->cb.off_v, w_first, 1, &slot, st));
+    const size_t M = (size_t)s->cb.nu * s->cb.nv;
+    if (y && y != s->y) PCAS_CUDA(cudaMemcpyAsync(s->y, y, M * sizeof(float), cudaMemcpyDefault, st));
+    PCAS_CUDA(cudaGraphLaunch(s->exec, st));
+    PCAS_CUDA(cudaMemcpyAsync(&s->h_out[slot], s->d_out, sizeof(SeqOut), cudaMemcpyDeviceToHost, st));
+    PCAS_CUDA(cudaEventRecord(s->ev[slot], st));
+    s->slot_ticket[slot] = s->next - 1;
+    s->slot_counted[slot] = false;
+    *ticket = s->next - 1;
+    return PCAS_OK;
+}
+
+int pcas_solver_seq_result(pcas_solver s, long long ticket, pcas_seq_result* out) {
+    PCAS_TRY(check_ptr(s, "solver"));
+    PCAS_TRY(check_ptr(out, "out"));
+    if (ticket < 0) return fail(PCAS_ERR_INVALID_ARG, "ticket must be >= 0");
+    const int slot = (int)(ticket % SEQ_RING);
+    if (s->slot_ticket[slot] != ticket)
+        return fail(PCAS_ERR_INVALID_ARG, "ticket %lld is not a pending or recent projection of a run", ticket);
+    PCAS_CUDA(cudaEventSynchronize(s->ev[slot]));
+    const SeqOut& h = s->h_out[slot];
+    for (int k = 0; k < PCAS_KMAX; k++) out->w[k] = k < s->K ? h.w[k] : 0.0;
+    for (int c = 0; c < 3; c++) out->c[c] = h.c[c];
+    out->loc_converged = h.c[3] != 0.0;
+    out->stats.iters = h.iters;
+    out->stats.evals = h.evals;
+    out->stats.status = h.phase == PH_SINGULAR ? PCAS_ERR_SINGULAR : PCAS_OK;
+    out->stats.J0 = h.J0;
+    out->stats.J = h.J;
+    out->stats.a = h.a;
+    out->stats.b = h.b;
+    out->stats.mu_last = h.mu;
+    if (!s->slot_counted[slot]) {
+        s->slot_counted[slot] = true;
+        std::lock_guard<std::mutex> lk(g_prof_mutex);
+        g_launches[PCAS_K_GRAPH] += h.launches;
+    }
+    return out->stats.status;
 }
 
 int pcas_solver_destroy(pcas_solver s) {
@@ -1628,13 +1853,17 @@ int pcas_batch_solve(pcas_batch b, const double* angle_rad, const double* w_init
     PCAS_TRY(check_ptr(w_init, "w_init"));
     const int n = (int)b->solvers.size();
     cudaStream_t st = as_stream(stream);
+    std::vector<int> slots(n);
     for (int i = 0; i < n; i++)
         PCAS_TRY(solver_stage(b->solvers[i], angle_rad[i], b->solvers[i]->cb.off_u, b->solvers[i]->cb.off_v,
-                              w_init + (size_t)i * PCAS_KMAX, st));
+                              w_init + (size_t)i * PCAS_KMAX, 0, &slots[i], st));
     PCAS_CUDA(cudaGraphLaunch(b->exec, st));
-    for (int i = 0; i < n; i++)
-        PCAS_CUDA(cudaMemcpyAsync(b->solvers[i]->h_state, b->solvers[i]->W.st, sizeof(SolveState),
-                                  cudaMemcpyDeviceToHost, st));
+    for (int i = 0; i < n; i++) {
+        pcas_solver si = b->solvers[i];
+        PCAS_CUDA(cudaMemcpyAsync(si->h_state, si->W.st, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
+        PCAS_CUDA(cudaEventRecord(si->ev[slots[i]], st));
+        si->seq_first = -1;
+    }
     PCAS_CUDA(cudaStreamSynchronize(st));
     int rc = PCAS_OK;
     long long launches = 0;

@@ -54,6 +54,11 @@ class Stats(C.Structure):
                 ("b", C.c_double), ("mu_last", C.c_double)]
 
 
+class SeqResult(C.Structure):
+    """pcas_seq_result: one projection of a run (include/pcasolve.h)."""
+    _fields_ = [("w", C.c_double * 8), ("c", C.c_double * 3), ("loc_converged", C.c_int), ("stats", Stats)]
+
+
 _D = C.POINTER(C.c_double)
 _P = C.c_void_p
 _lock = threading.Lock()
@@ -93,6 +98,9 @@ _SIGS = {
     "pcas_solver_solve": (C.c_int, [C.c_void_p, _P, C.c_double, C.c_double, C.c_double, _D, _D,
                                     C.POINTER(Stats), _P]),
     "pcas_solver_destroy": (C.c_int, [C.c_void_p]),
+    "pcas_solver_seq_begin": (C.c_int, [C.c_void_p, _D, C.c_int, _D, C.c_int, C.c_double, _D, C.c_int, _P]),
+    "pcas_solver_seq_enqueue": (C.c_int, [C.c_void_p, _P, C.c_double, _D, C.POINTER(C.c_longlong), _P]),
+    "pcas_solver_seq_result": (C.c_int, [C.c_void_p, C.c_longlong, _P]),
     "pcas_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                     C.c_int, _P]),
     "pcas_batch_solve": (C.c_int, [C.c_void_p, _D, _D, _D, C.POINTER(Stats), _P]),
@@ -451,6 +459,60 @@ class Solver:
                                        w0.ctypes.data_as(_D), w_out.ctypes.data_as(_D), C.byref(st),
                                        _stream(stream)))
         return w_out, {k: getattr(st, k) for k, _ in Stats._fields_}
+
+    # ---- runs of consecutive projections (warm start and localisation on the device)
+    def seq_begin(self, lp_coef, c_ref, loc_max_iter=50, loc_tol_mm=1e-6, w_hist=None, stream=None):
+        """Starts a run.  lp_coef: (K, L) Eq. (3) coefficients (lp_fit); c_ref:
+        tumour centroid of the reference CT (mm); w_hist: (n, K) solutions
+        before the run, latest first (or None)."""
+        c = np.ascontiguousarray(lp_coef, dtype=np.float64)
+        if c.ndim != 2 or c.shape[0] != self.K:
+            raise ValueError(f"lp_coef must be (K={self.K}, L)")
+        cr = _host_d(c_ref, 3)
+        if w_hist is None or len(w_hist) == 0:
+            h, n = None, 0
+        else:
+            h = np.ascontiguousarray(w_hist, dtype=np.float64).reshape(-1, self.K)
+            n = h.shape[0]
+        _check(lib().pcas_solver_seq_begin(self.h, c.ctypes.data_as(_D), c.shape[1], cr.ctypes.data_as(_D),
+                                           int(loc_max_iter), float(loc_tol_mm),
+                                           None if h is None else h.ctypes.data_as(_D), n, _stream(stream)))
+
+    def seq_enqueue(self, y, angle, w_first=None, stream=None):
+        """Queues one projection (y: float32 tensor on the device or in pinned
+        host memory); returns its ticket without waiting."""
+        nu, nv = self.cb.nu, self.cb.nv
+        if y is None or not y.is_contiguous() or y.numel() != nu * nv or str(y.dtype) != "torch.float32":
+            raise ValueError(f"y must be a contiguous float32 tensor of {nu * nv} values")
+        if not (y.is_cuda or y.is_pinned()):
+            raise ValueError("y must live on the device or in pinned host memory")
+        wf = None if w_first is None else _host_d(w_first, self.K)
+        t = C.c_longlong()
+        _check(lib().pcas_solver_seq_enqueue(self.h, y.data_ptr(), float(angle),
+                                             None if wf is None else wf.ctypes.data_as(_D), C.byref(t),
+                                             _stream(stream)))
+        return t.value
+
+    def seq_result(self, ticket):
+        """Waits for a queued projection; returns (w (K,), stats dict, c (3,), converged)."""
+        r = SeqResult()
+        _check(lib().pcas_solver_seq_result(self.h, int(ticket), C.byref(r)))
+        stats = {k: getattr(r.stats, k) for k, _ in Stats._fields_}
+        return np.array(r.w[:self.K]), stats, np.array(r.c[:]), bool(r.loc_converged)
+
+    def solve_sequence(self, ys, angles, w_first=None, lookahead=32, stream=None):
+        """Queues every projection of ys (indexable, one tensor per angle) in
+        the current run, keeping at most ``lookahead`` in flight; returns the
+        list of seq_result tuples in order."""
+        lookahead = max(1, min(int(lookahead), 48))
+        tickets, out = [], []
+        for t in range(len(angles)):
+            tickets.append(self.seq_enqueue(ys[t], angles[t], w_first, stream))
+            if len(tickets) - len(out) >= lookahead:
+                out.append(self.seq_result(tickets[len(out)]))
+        while len(out) < len(tickets):
+            out.append(self.seq_result(tickets[len(out)]))
+        return out
 
     def close(self):
         if getattr(self, "h", None):
