@@ -293,6 +293,29 @@ __device__ __forceinline__ float tri_halo(const float* __restrict__ f, const Gri
     return fmaf(zz, c1 - c0, c0);
 }
 
+// Whether any cell taps_halo may take for a position in the box [lo, hi]
+// (per axis) lies in a marked brick of the reference CT (m: its bricks).
+// The clamped brick coordinate is monotone in the position, so the cells of
+// the box's positions lie in the bricks between those of its corners; a box
+// spanning more than two bricks along an axis is reported live.
+__device__ __forceinline__ bool f0_box_live(const unsigned char* __restrict__ m, const Grid& g, float lox,
+                                            float loy, float loz, float hix, float hiy, float hiz) {
+    const int nbx = occ_n(g.nx), nby = occ_n(g.ny), nbz = occ_n(g.nz);
+    auto br = [](float q, int n, int nb) {
+        q = fminf(fmaxf(q, -2.0f), (float)n + 1.0f);
+        return min(max(((int)floorf(q) + 1) >> 3, 0), nb - 1);
+    };
+    const int x0 = br(lox, g.nx, nbx), x1 = br(hix, g.nx, nbx);
+    const int y0 = br(loy, g.ny, nby), y1 = br(hiy, g.ny, nby);
+    const int z0 = br(loz, g.nz, nbz), z1 = br(hiz, g.nz, nbz);
+    if (x1 - x0 > 1 || y1 - y0 > 1 || z1 - z0 > 1) return true;
+    for (int z = z0; z <= z1; z++)
+        for (int y = y0; y <= y1; y++)
+            for (int x = x0; x <= x1; x++)
+                if (__ldg(m + (z * nby + y) * nbx + x)) return true;
+    return false;
+}
+
 // tri_halo, or +0 without touching the taps when the cell's brick of the
 // reference CT is empty (m: its bricks, or null).  The same bits either way.
 __device__ __forceinline__ float tri_halo_m(const float* __restrict__ f, const unsigned char* __restrict__ m,

@@ -260,11 +260,32 @@ k_warp_batch(const float* __restrict__ f0h, const T* __restrict__ mean,
             for (int c = 0; c < 3; c++)
 #pragma unroll
                 for (int b = 0; b < TRIAL_BATCH; b++) x[b][c] = fmaf(wk[b][kk], u[kk][c], x[b][c]);
+        float q[TRIAL_BATCH][3];
+#pragma unroll
+        for (int b = 0; b < TRIAL_BATCH; b++) {
+            q[b][0] = fmaf(x[b][0], g.inv_sx, (float)i);
+            q[b][1] = fmaf(x[b][1], g.inv_sy, (float)j);
+            q[b][2] = fmaf(x[b][2], g.inv_sz, (float)k);
+        }
+        // one test for the five: when every brick their cells can lie in is
+        // empty, all eight taps of each are zero and so are the candidates
+        bool live = true;
+        if (occ.f0m) {
+            float lo[3], hi[3];
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                lo[c] = hi[c] = q[0][c];
+#pragma unroll
+                for (int b = 1; b < TRIAL_BATCH; b++) {
+                    lo[c] = fminf(lo[c], q[b][c]);
+                    hi[c] = fmaxf(hi[c], q[b][c]);
+                }
+            }
+            live = f0_box_live(occ.f0m, g, lo[0], lo[1], lo[2], hi[0], hi[1], hi[2]);
+        }
         float o[TRIAL_BATCH];
 #pragma unroll
-        for (int b = 0; b < TRIAL_BATCH; b++)
-            o[b] = tri_halo_m(f0h, occ.f0m, g, fmaf(x[b][0], g.inv_sx, (float)i),
-                               fmaf(x[b][1], g.inv_sy, (float)j), fmaf(x[b][2], g.inv_sz, (float)k));
+        for (int b = 0; b < TRIAL_BATCH; b++) o[b] = live ? tri_halo(f0h, g, q[b][0], q[b][1], q[b][2]) : 0.0f;
         const int a0 = swp ? j : i, a1 = swp ? i : j;
         const long d = pad_index(pd, a0, a1, k);
         fpad4[d] = make_float4(o[0], o[1], o[2], o[3]);
