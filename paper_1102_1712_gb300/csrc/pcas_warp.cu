@@ -106,16 +106,21 @@ template <typename T>
 __global__ void __launch_bounds__(kWarpThreads)
 k_fill_f0h(const T* __restrict__ f0, Grid g, float* __restrict__ f0h, unsigned char* __restrict__ f0m) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
-    if (i >= g.nx) return;
-    const long sy = g.nx + 2 * F0_HALO, sz = sy * (g.ny + 2 * F0_HALO);
-    const float v = ldg_f(f0 + ((long)k * g.ny + j) * g.nx + i);
-    f0h[(k + F0_HALO) * sz + (j + F0_HALO) * sy + (i + F0_HALO)] = v;
-    if (f0m && v != 0.0f) {
-        const int nbx = occ_n(g.nx), nby = occ_n(g.ny);
-        for (int bz = k >> 3; bz <= (k + 1) >> 3; bz++)
-            for (int by = j >> 3; by <= (j + 1) >> 3; by++)
-                for (int bx = i >> 3; bx <= (i + 1) >> 3; bx++) f0m[(bz * nby + by) * nbx + bx] = 1;
+    float v = 0.0f;
+    if (i < g.nx) {
+        const long sy = g.nx + 2 * F0_HALO, sz = sy * (g.ny + 2 * F0_HALO);
+        v = ldg_f(f0 + ((long)k * g.ny + j) * g.nx + i);
+        f0h[(k + F0_HALO) * sz + (j + F0_HALO) * sy + (i + F0_HALO)] = v;
     }
+    if (!f0m) return;
+    // the warp's span of non-zero voxels along the row, marked by one lane
+    int lo = __reduce_min_sync(0xffffffffu, v != 0.0f ? i : INT_MAX);
+    int hi = __reduce_max_sync(0xffffffffu, v != 0.0f ? i : INT_MIN);
+    if ((threadIdx.x & 31) != 0 || lo > hi) return;
+    const int nbx = occ_n(g.nx), nby = occ_n(g.ny);
+    for (int bz = k >> 3; bz <= (k + 1) >> 3; bz++)
+        for (int by = j >> 3; by <= (j + 1) >> 3; by++)
+            for (int bx = lo >> 3; bx <= (hi + 1) >> 3; bx++) f0m[(bz * nby + by) * nbx + bx] = 1;
 }
 
 // Occupancy bricks of the solver frame (see Occ): the frame exchanges x and y
