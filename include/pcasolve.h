@@ -250,6 +250,8 @@ int pcas_solver_destroy(pcas_solver solver);
  *   its solution, centroid and statistics (host); valid for the last 64
  *   tickets of the solver.  Returns PCAS_ERR_SINGULAR for a constant image
  *   (the run goes on from the unchanged start).
+ * Within a run the reference CT is read once, by the run's first projection
+ * (its halo copy is kept for the rest): it must not change during a run.
  * A pcas_solver_solve or batch solve in between ends the run. */
 typedef struct {
     double w[PCAS_KMAX];      /* solution (first K entries) */

@@ -481,7 +481,7 @@ int check_finite(const double* v, int n, const char* name) {
 // then filled).
 int stage_f0h(const void* f0, int dt, const Grid& g, const Ws& W, const Tune& T, cudaStream_t s) {
     PCAS_CUDA(cudaMemsetAsync(W.f0h, 0, W.f0h_bytes, s));
-    PCAS_LAUNCH(PCAS_K_INIT, s, launch_fill_f0h(f0, dt, g, W.f0h, T.skip ? W.f0m : nullptr, s));
+    PCAS_LAUNCH(PCAS_K_INIT, s, launch_fill_f0h(f0, dt, g, W.f0h, T.skip ? W.f0m : nullptr, nullptr, s));
     return PCAS_OK;
 }
 
@@ -1287,7 +1287,8 @@ struct SeqBlock {
     double c_ref[3], loc_tol;
     double o[3], is[3];               // volume origin and reciprocal spacing
     int L, loc_max_iter;
-    int n, pad;                       // solutions in the history (n >= L: full predictor)
+    int n;                            // solutions in the history (n >= L: full predictor)
+    int f0_ready;                     // the run's first projection has copied the reference CT
     double hist[LP_MAX][PCAS_KMAX];
 };
 
@@ -1313,6 +1314,7 @@ __device__ double seq_start(const SeqBlock* sq, const InitBlock* ib, int k) {
 
 __global__ void k_init_dev(SolveState* st, const InitBlock* __restrict__ ib, const SeqBlock* __restrict__ sq) {
     if (threadIdx.x != 0) return;
+    st->keep_f0h = ib->seq && sq->f0_ready;   // a run reads the reference CT once
     for (int k = 0; k < PCAS_KMAX; k++) {
         st->w[k] = k < ib->K ? (ib->seq ? seq_start(sq, ib, k) : ib->w[k]) : 0.0;
         st->d[k] = 0.0;
@@ -1373,6 +1375,7 @@ __global__ void k_seq_end(SolveState* st, const InitBlock* __restrict__ ib, SeqB
         for (int k = 0; k < PCAS_KMAX; k++) sq->hist[l][k] = sq->hist[l - 1][k];
     for (int k = 0; k < PCAS_KMAX; k++) sq->hist[0][k] = w[k];
     if (sq->n < LP_MAX) sq->n += 1;
+    sq->f0_ready = 1;
     st->launches += 1;
     for (int k = 0; k < PCAS_KMAX; k++) out->w[k] = w[k];
     for (int i = 0; i < 4; i++) out->c[i] = c[i];
@@ -1489,7 +1492,9 @@ int capture_solve(pcas_solver s, cudaGraph_t graph, cudaStream_t cs, const float
     k_init_dev<<<1, 32, 0, cs>>>(W.st, &s->d_stage->ib, s->d_seq);
     PCAS_G(cudaGetLastError());
     const Occ oc = occ_of(W, s->tune);
-    PCAS_G(launch_fill_f0h(s->f0, s->dtype, g, W.f0h, s->tune.skip ? W.f0m : nullptr, cs));  // f0 may change
+    // the reference CT is copied for every solve, except after the first
+    // projection of a run (k_init_dev sets keep_f0h then)
+    PCAS_G(launch_fill_f0h(s->f0, s->dtype, g, W.f0h, s->tune.skip ? W.f0m : nullptr, &W.st->keep_f0h, cs));
     WSrc wcur{};
     wcur.dev = W.st->w;
     wcur.phase = &W.st->phase;

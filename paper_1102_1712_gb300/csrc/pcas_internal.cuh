@@ -106,6 +106,7 @@ struct SolveState {
     // projector that consumes the volume.
     int box[2][6];
     unsigned int occ_gen;                 // pass number of the occupancy bricks (never reset)
+    int keep_f0h;                         // device-driven run: the halo copy of f0 is current
 };
 
 enum : int { BOX_EMPTY = 0x3fffffff };
@@ -568,7 +569,9 @@ cudaError_t launch_warp_dvf(const void* f0, int dt, const float* dvf, Grid g, fl
 // Copies f0 (storage type dt) into the interior of the halo copy f0h (whose
 // halo the caller has zeroed; it is never written).
 // f0m (may be null): bricks of the reference CT, zeroed by the caller, marked here.
-cudaError_t launch_fill_f0h(const void* f0, int dt, Grid g, float* f0h, unsigned char* f0m, cudaStream_t s);
+// skip (device, may be null): the copy is skipped while *skip is non-zero.
+cudaError_t launch_fill_f0h(const void* f0, int dt, Grid g, float* f0h, unsigned char* f0m, const int* skip,
+                            cudaStream_t s);
 // Solver warps: launch_warp_pca writes f(w_src) to the scalar zero-halo
 // buffer; launch_warp_batch writes the batch: candidates st->wt[0..3]
 // interleaved (float4) and wt[4] to fpad.

@@ -101,26 +101,36 @@ k_warp_dvf(const T* __restrict__ f0, const float* __restrict__ dvf, Grid g, long
 
 // The halo copy of the reference CT (see tri_halo): interior only.  With f0m
 // it marks the bricks whose taps include a non-zero voxel (see Occ): voxel i
-// is a tap of the cells of bricks i >> 3 and (i + 1) >> 3 along each axis.
+// is a tap of the cells of bricks i >> 3 and (i + 1) >> 3 along each axis;
+// one lane per warp marks the span of the warp's non-zero voxels of a row.
+// Blocks stride over the rows (j, k).  skip (may be null): when it holds a
+// non-zero value the copy is current and the kernel returns at once.
 template <typename T>
 __global__ void __launch_bounds__(kWarpThreads)
-k_fill_f0h(const T* __restrict__ f0, Grid g, float* __restrict__ f0h, unsigned char* __restrict__ f0m) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
-    float v = 0.0f;
-    if (i < g.nx) {
-        const long sy = g.nx + 2 * F0_HALO, sz = sy * (g.ny + 2 * F0_HALO);
-        v = ldg_f(f0 + ((long)k * g.ny + j) * g.nx + i);
-        f0h[(k + F0_HALO) * sz + (j + F0_HALO) * sy + (i + F0_HALO)] = v;
-    }
-    if (!f0m) return;
-    // the warp's span of non-zero voxels along the row, marked by one lane
-    int lo = __reduce_min_sync(0xffffffffu, v != 0.0f ? i : INT_MAX);
-    int hi = __reduce_max_sync(0xffffffffu, v != 0.0f ? i : INT_MIN);
-    if ((threadIdx.x & 31) != 0 || lo > hi) return;
+k_fill_f0h(const T* __restrict__ f0, Grid g, float* __restrict__ f0h, unsigned char* __restrict__ f0m,
+           const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    const long sy = g.nx + 2 * F0_HALO, sz = sy * (g.ny + 2 * F0_HALO);
     const int nbx = occ_n(g.nx), nby = occ_n(g.ny);
-    for (int bz = k >> 3; bz <= (k + 1) >> 3; bz++)
-        for (int by = j >> 3; by <= (j + 1) >> 3; by++)
-            for (int bx = lo >> 3; bx <= (hi + 1) >> 3; bx++) f0m[(bz * nby + by) * nbx + bx] = 1;
+    const int rows = g.ny * g.nz;
+    for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int j = r % g.ny, k = r / g.ny;
+        for (int i0 = 0; i0 < g.nx; i0 += blockDim.x) {      // the same trip count for every lane
+            const int i = i0 + threadIdx.x;
+            float v = 0.0f;
+            if (i < g.nx) {
+                v = ldg_f(f0 + ((long)k * g.ny + j) * g.nx + i);
+                f0h[(k + F0_HALO) * sz + (j + F0_HALO) * sy + (i + F0_HALO)] = v;
+            }
+            if (!f0m) continue;
+            const int lo = __reduce_min_sync(0xffffffffu, v != 0.0f ? i : INT_MAX);
+            const int hi = __reduce_max_sync(0xffffffffu, v != 0.0f ? i : INT_MIN);
+            if ((threadIdx.x & 31) != 0 || lo > hi) continue;
+            for (int bz = k >> 3; bz <= (k + 1) >> 3; bz++)
+                for (int by = j >> 3; by <= (j + 1) >> 3; by++)
+                    for (int bx = lo >> 3; bx <= (hi + 1) >> 3; bx++) f0m[(bz * nby + by) * nbx + bx] = 1;
+        }
+    }
 }
 
 // Occupancy bricks of the solver frame (see Occ): the frame exchanges x and y
@@ -385,9 +395,11 @@ cudaError_t launch_warp_dvf(const void* f0, int dt, const float* dvf, Grid g, fl
                           cudaGetLastError()))
 }
 
-cudaError_t launch_fill_f0h(const void* f0, int dt, Grid g, float* f0h, unsigned char* f0m, cudaStream_t s) {
-    const RowLaunch L = row_launch(g, 1);
-    PCAS_DT_DISPATCH(dt, (k_fill_f0h<T><<<L.grid, L.threads, 0, s>>>(static_cast<const T*>(f0), g, f0h, f0m),
+cudaError_t launch_fill_f0h(const void* f0, int dt, Grid g, float* f0h, unsigned char* f0m, const int* skip,
+                            cudaStream_t s) {
+    const int rows = g.ny * g.nz;
+    const unsigned nb = (unsigned)(rows < 1216 ? rows : 1216);     // 8 blocks per SM of a GB300
+    PCAS_DT_DISPATCH(dt, (k_fill_f0h<T><<<nb, kWarpThreads, 0, s>>>(static_cast<const T*>(f0), g, f0h, f0m, skip),
                           cudaGetLastError()))
 }
 
