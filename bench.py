@@ -449,7 +449,15 @@ def run_ours(args, ws_, rank, local):
                 "d2h_bytes_per_step": SEQ_OUT_BYTES},
     }
     if ws_ == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(vol, f0, c_ref, U, trace, train, angles, ys, W_)
+        line["cpu_baseline"], o = cpu_baseline(vol, f0, c_ref, U, trace, train, angles, ys, W_)
+        # the same projection from the same start on the GPU: parity at full size
+        w_g, st_g = P.solve_projection(tf0, None, tU, ys[W_], vol, view(angles[W_]), o["w0"], prm, ws=wsp)
+        c_g, _ = P.localize_tumor(None, tU, w_g, vol, c_ref)
+        line["oracle_parity"] = {"projection": W_, "w_max_abs_diff": float(np.abs(w_g - o["w"]).max()),
+                                 "centroid_diff_mm": float(np.linalg.norm(c_g - o["c"])),
+                                 "J_rel_diff": float(abs(st_g["J"] - o["J"]) / o["J"]),
+                                 "iters_gpu_oracle": [st_g["iters"], o["iters"]],
+                                 "evals_gpu_oracle": [st_g["evals"], o["evals"]]}
     return line
 
 
@@ -469,11 +477,13 @@ def cpu_baseline(vol, f0, c_ref, U, trace, train, angles, ys, t):
     y = ys[t].cpu().numpy()
     t0 = time.perf_counter()
     w, st, _ = oracle_solve_one(O, vol, f0, U, y, angles[t], w0, step_mm())
-    O.localize_tumor(None, U, w, vol, c_ref)
+    c, _ = O.localize_tumor(None, U, w, vol, c_ref)
     dt = time.perf_counter() - t0
-    return {"value": round(1.0 / dt, 5), "unit": "projections/s", "cores": os.cpu_count(), "kind": "oracle",
+    line = {"value": round(1.0 / dt, 5), "unit": "projections/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"1 projection (#{t}) of the same workload, full solve ({st['iters']} iterations, "
                       f"{st['evals']} evaluations) + localisation, {dt:.1f} s"}
+    return line, {"w0": w0, "w": np.asarray(w), "c": np.asarray(c), "J": st["J"], "iters": st["iters"],
+                  "evals": st["evals"]}
 
 
 def run_reference(args, ws_, rank):
