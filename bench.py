@@ -430,6 +430,8 @@ def run_ours(args, ws_, rank, local):
                      "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": kernels[dom]["frac_hbm"],
                      "traffic": ncu_traffic(dom), "peak_source": pk_kind,
                      "l1_pipe_frac": ncu_field(dom, "l1tex_throughput_frac", float),
+                     "smem_wavefront_frac": ncu_field(dom, "smem_wavefront_frac", float),
+                     "issue_active_frac": ncu_field(dom, "issue_active_frac", float),
                      "path_alg_gbs": round(total_alg / (ms_host / 1e3) / 1e9, 1),
                      "path_frac": round(total_alg / (ms_host / 1e3) / 1e9 / pk["hbm_gbs"], 4),
                      "note": "kernel durations from CUDA events in the host-driven pass over the same "
