@@ -431,6 +431,7 @@ __global__ void k_init_state(SolveState* st, int K, double w0, double w1, double
     st->K = K; st->max_trials = max_trials;
     st->cur = 0; st->phase = PH_RUNNING; st->evals = 0; st->trials = 0;
     st->nvalid = 0; st->iters = 0; st->batches = 0; st->max_iter = max_iter; st->launches = 0;
+    st->wide = 1;
     for (int i = 0; i < 4; i++) st->counter[i] = 0u;
     for (int i = 0; i < 2; i++)
         for (int j = 0; j < 6; j++) st->box[i][j] = BOX_EMPTY;
@@ -535,27 +536,13 @@ int solve_host(const void* f0, const void* mean, const void* U, int dtype, int K
         PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
                     launch_adjoint_grad(W.rayt, g, W.view, W.f0h, occ_of(W, T).f0m, mean, U, dtype, K, 1, W.st,
                                         W.part_adj, W.adj, T.vt, adj_blocks, 0ull, 0, nullptr, s));
-        // Armijo backtracking over the schedule mu0, beta mu0, ...: the next (up
-        // to five) step sizes that the rule may still try are rendered and
-        // tested in one pass; the device accepts the first that passes, in
-        // order.  The host mirrors the schedule only to size each batch, and
-        // reads one flag per batch.
-        double mu_t = prm->mu0;
-        int t = 0;
+        // Armijo backtracking over the schedule mu0, beta mu0, ...: the next
+        // step sizes that the rule may still try (up to five, two after an
+        // iteration that took its first one) are rendered and tested in one
+        // pass; the device accepts the first that passes, in order, and stops
+        // when the schedule is spent.  The host reads one flag per batch.
         phase = PH_RUNNING;
         for (int batch = 0; batch <= prm->max_trials; batch++) {    // each batch tries >= 1 step
-            int nvalid = 0;
-            double m = mu_t;
-            while (nvalid < TRIAL_BATCH && m >= prm->mu_min && t + nvalid < prm->max_trials) {
-                nvalid++;
-                m *= prm->beta;
-            }
-            if (nvalid == 0) {          // nothing left to try: the device has stopped too
-                PCAS_CUDA(cudaMemcpyAsync(&phase, &W.st->phase, sizeof(int), cudaMemcpyDeviceToHost, s));
-                PCAS_CUDA(cudaStreamSynchronize(s));
-                if (phase == PH_RUNNING) phase = PH_STOP;
-                break;
-            }
             PCAS_LAUNCH(PCAS_K_WARP_BATCH, s, launch_warp_batch(W.f0h, mean, U, dtype, K, W.st, g, W.view,
                                                                 W.fpad4, W.fpad, occ_of(W, T), s));
             PCAS_LAUNCH(PCAS_K_DRR_BATCH, s,
@@ -564,9 +551,8 @@ int solve_host(const void* f0, const void* mean, const void* U, int dtype, int K
             PCAS_CUDA(cudaMemcpyAsync(&phase, &W.st->phase, sizeof(int), cudaMemcpyDeviceToHost, s));
             PCAS_CUDA(cudaStreamSynchronize(s));
             if (phase != PH_RUNNING) break;
-            t += nvalid;
-            mu_t = m;
         }
+        if (phase == PH_RUNNING) phase = PH_STOP;     // batch cap reached without a decision
         if (phase == PH_ACCEPT || phase == PH_STOP) iters++;
         if (phase != PH_ACCEPT) break;
     }
@@ -1330,6 +1316,7 @@ __global__ void k_init_dev(SolveState* st, const InitBlock* __restrict__ ib, con
     st->K = ib->K; st->max_trials = ib->max_trials; st->max_iter = ib->max_iter;
     st->cur = 0; st->phase = PH_RUNNING; st->evals = 0; st->trials = 0;
     st->nvalid = 0; st->iters = 0; st->batches = 0; st->launches = 1;
+    st->wide = 1;
     for (int i = 0; i < 4; i++) st->counter[i] = 0u;
     for (int i = 0; i < 2; i++)
         for (int j = 0; j < 6; j++) st->box[i][j] = BOX_EMPTY;

@@ -96,6 +96,8 @@ struct SolveState {
     int cur;                              // buffer holding P f(w)
     int phase, evals, trials;
     int nvalid;                           // candidates of the pending batch still on the schedule
+    int wide;                             // 0: the last iteration took its first step size, so the
+                                          // next iteration's first batch renders two candidates
     int iters, batches;                   // device-driven solve: completed iterations, batches this iteration
     int max_iter, launches;               // launches: kernels run by a device-driven solve
     unsigned int counter[4];              // last-block counters (reset by the last block)

@@ -230,7 +230,10 @@ k_warp_pca(const float* __restrict__ f0h, const T* __restrict__ mean,
 // the single-volume warp, so a candidate's volume is bit-identical to a lone
 // evaluation.  Output: one float4 (f_0..f_3) per voxel in the candidate
 // buffer and f_4 in the one-volume buffer, zero-halo layout; the occupancy
-// bricks mark the union of the five.
+// bricks mark the union of the five.  All five are rendered even when fewer
+// are on the schedule (a narrow batch projects only the first two): the
+// kernel is issue-bound, and a run-time candidate count in it costs more
+// than the gathers it would save.
 template <typename T, int KT>
 __global__ void __launch_bounds__(kWarpThreads, KT <= 3 ? 6 : (KT <= 5 ? 5 : (KT <= 7 ? 4 : 3)))
 k_warp_batch(const float* __restrict__ f0h, const T* __restrict__ mean,
