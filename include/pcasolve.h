@@ -174,9 +174,10 @@ int cost_grad_static(const float* f0, const float* mean, const float* U, int K, 
  * the solve ends.  It also ends after max_iter iterations or at G = 0.
  * f0, mean, U, y, ws: device; w_init, w_out (K), params, stats: host.
  * The backtracking candidates are evaluated up to five at a time (one warp and
- * one projection pass for all of them) and tested in schedule order, so the
- * accepted step is the one the one-at-a-time rule would take; stats->evals
- * counts evaluations as that rule would.  Synchronous (one host read of a
+ * one projection pass for all of them; two when the previous iteration took
+ * its first step size) and tested in schedule order, so the accepted step is
+ * the one the one-at-a-time rule would take; stats->evals counts evaluations
+ * as that rule would.  Synchronous (one host read of a
  * 4-byte flag per batch of candidates). */
 int solve_projection(const float* f0, const float* mean, const float* U, int K, const float* y,
                      const pcas_vol* vol, const pcas_cb* cb, const double* w_init,
