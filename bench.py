@@ -402,6 +402,13 @@ def run_ours(args, ws_, rank, local):
                              "achieved_gbs": round(gbs, 1), "frac_hbm": round(gbs / pk["hbm_gbs"], 4)}
     dom = max(kernels, key=lambda k: kernels[k]["total_ms"])
     launches = launches_timed
+    # the whole path in the one-at-a-time accounting of the method: per
+    # projection iters gradient evaluations of B_g bytes and (evals - 1) trial
+    # evaluations of B_t bytes, over the device-driven run's time
+    B_g = (24 * (K + 1) + 12) * N + 16 * M
+    B_t = (12 * (K + 1) + 12) * N + 4 * M
+    B_path = float(np.sum(iters * B_g + (evals - 1) * B_t))
+    path_run_gbs = B_path / (ms / 1e3) / 1e9
     total_alg = sum(kernels[k]["alg_bytes"] * kernels[k]["launches"] for k in kernels)
     line = {
         "metric": METRIC,
@@ -434,6 +441,10 @@ def run_ours(args, ws_, rank, local):
                      "issue_active_frac": ncu_field(dom, "issue_active_frac", float),
                      "path_alg_gbs": round(total_alg / (ms_host / 1e3) / 1e9, 1),
                      "path_frac": round(total_alg / (ms_host / 1e3) / 1e9 / pk["hbm_gbs"], 4),
+                     "run_path_gbs": round(path_run_gbs, 1),
+                     "run_path_frac": round(path_run_gbs / pk["hbm_gbs"], 4),
+                     "run_path_bytes": "per projection iters * ((24(K+1)+12)N + 16M) + (evals-1) * "
+                                       "((12(K+1)+12)N + 4M), over the device-driven run's time",
                      "note": "kernel durations from CUDA events in the host-driven pass over the same "
                              "projections (graph launches cannot be bracketed per kernel)"},
         "host_driven": {"value": round(K_ / (ms_host / 1e3), 3), "ms_per_step": round(ms_host / K_, 4)},
