@@ -58,10 +58,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--irregular", action="store_true", help="irregular breathing trace")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="sequence", choices=["sequence", "fluoro", "precision", "batch"],
+    ap.add_argument("--workload", default="sequence",
+                    choices=["sequence", "fluoro", "precision", "batch", "oracle"],
                     help="sequence: the default line; fluoro: the same sequence at one fixed gantry angle "
                          "(fluoroscopy); precision: float32 vs bfloat16 vs float16 storage; "
-                         "batch: 64 uneven solves in one graph launch vs one after another")
+                         "batch: 64 uneven solves in one graph launch vs one after another; "
+                         "oracle: the FP64 oracle's timings on the host cores (no GPU work)")
     ap.add_argument("--projector", default="siddon", choices=["siddon", "trilinear"],
                     help="renderer of the measured images: Siddon's exact path (Sec. II.B, no inverse "
                          "crime) or the solver's own trilinear projector")
@@ -787,6 +789,81 @@ def run_batch(args, local):
             "gpu_launches": launches, "clocks": clk.summary()}
 
 
+# ------------------------------------------------------- oracle timings per config
+def run_oracle_timing(args):
+    """The FP64 oracle on the host cores: per evaluation (cost_grad, median of
+    three) on the tiny, sequence and precision volumes, and per projection
+    (full solve + localisation) on the tiny case and on --steps projections of
+    the sequence (every 30th from #5, warm-started from the prediction of the
+    planted coefficients).  Measured images rendered by the oracle's Siddon
+    projector.  Bounded: a few minutes on 16 cores."""
+    import oracle as O
+    from paper_1102_1712_gb300 import synth as S
+    O.build()
+
+    def med3(fn):
+        ts = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            fn()
+            ts.append(time.perf_counter() - t0)
+        return float(np.median(ts))
+
+    out = {"impl": "oracle-timing", "kind": "oracle", "cores": os.cpu_count(), "unit": "s"}
+    # tiny: 64x64x32 at 4 mm, K = 3, 128x96 at 3.1 mm, 20 iterations from w = 0
+    vol = S.volume(64, 64, 32, 4.0, 4.0, 4.0)
+    f0, c_ref = S.phantom(vol, 15.0, seed=1)
+    U = S.eigen_dvfs(vol, 3, seed=2)
+    cb = S.cone_beam(128, 96, 3.1, 3.1, 0.0)
+    w_true = np.array([1.2, -0.4, 0.3])
+    y = O.siddon_forward(O.warp_volume(f0, O.pca_dvf(None, U, w_true, vol), vol), vol, cb)
+    y = (y + S.gaussian_noise(y.shape, 0.01 * np.abs(y).max(), seed=3, dtype=np.float64)).astype(np.float32)
+    prm = dict(mu0=0.2, alpha=0.1, beta=0.5, mu_min=0.01, max_iter=20, max_trials=30, step=2.0)
+    t_eval = med3(lambda: O.cost_grad(f0, None, U, 0.5 * w_true, y, vol, cb, 2.0))
+    t0 = time.perf_counter()
+    _, st, _ = O.solve_projection(f0, None, U, y, vol, cb, np.zeros(3), prm)
+    O.localize_tumor(None, U, _, vol, c_ref)
+    out["tiny"] = {"eval_s": round(t_eval, 4), "projection_s": round(time.perf_counter() - t0, 3),
+                   "iters": st["iters"], "evals": st["evals"]}
+    # sequence: 256x256x100, K = 3, 512x384
+    vol, f0, c_ref, U, trace, train, angles = make_inputs(False)
+    step = step_mm()
+    c_lp = O.lp_fit(train, 2)
+    ts = [5 + 30 * i for i in range(max(1, args.steps))]
+    y0 = None
+    proj = []
+    for t in ts:
+        f = O.warp_volume(f0, O.pca_dvf(None, U, trace[t], vol), vol)
+        y = O.siddon_forward(f, vol, view(angles[t]))
+        y = (y + S.gaussian_noise(y.shape, WORKLOAD["noise"] * np.abs(y).max(),
+                                  seed=1000 * WORKLOAD["seeds"]["noise"] + t, dtype=np.float64)).astype(np.float32)
+        if y0 is None:
+            y0 = (y, t)
+        w0 = O.lp_predict(np.stack([trace[t - 1], trace[t - 2]]), c_lp)
+        t0 = time.perf_counter()
+        w, st, _ = oracle_solve_one(O, vol, f0, U, y, angles[t], w0, step)
+        O.localize_tumor(None, U, w, vol, c_ref)
+        proj.append({"projection": t, "s": round(time.perf_counter() - t0, 3), "iters": st["iters"],
+                     "evals": st["evals"]})
+    y, t = y0
+    t_eval = med3(lambda: O.cost_grad(f0, None, U, trace[t], y, vol, view(angles[t]), step))
+    out["sequence"] = {"eval_s": round(t_eval, 3), "projections": proj,
+                       "projections_per_s": round(len(proj) / sum(p["s"] for p in proj), 5)}
+    # precision volume: 512x512x160 at 1x1x2 mm, K = 5, 1024x768 (one evaluation)
+    W = PRECISION
+    vol = S.volume(*W["vol"])
+    f0, c_ref = S.phantom(vol, W["tumor_mm"], seed=W["seeds"]["phantom"])
+    U = S.eigen_dvfs(vol, W["K"], seed=W["seeds"]["dvf"], coarse=(2, 4, 4))
+    d = W["det"]
+    cb = S.cone_beam(d[0], d[1], d[2], d[3], 0.4)
+    w5 = np.array([1.0, 0.3, 0.15, 0.1, -0.05])
+    y = O.siddon_forward(O.warp_volume(f0, O.pca_dvf(None, U, w5, vol), vol), vol, cb).astype(np.float32)
+    t0 = time.perf_counter()
+    O.cost_grad(f0, None, U, 0.8 * w5, y, vol, cb, 0.5 * min(W["vol"][3:]))
+    out["precision"] = {"eval_s": round(time.perf_counter() - t0, 3)}
+    return out
+
+
 def main():
     args = parse()
     ws_, rank, local = dist_env()
@@ -799,6 +876,8 @@ def main():
         line = run_precision(args, local) if rank == 0 else None
     elif args.workload == "batch":
         line = run_batch(args, local) if rank == 0 else None
+    elif args.workload == "oracle":
+        line = run_oracle_timing(args) if rank == 0 else None
     else:
         line = run_ours(args, ws_, rank, local)
     if line is not None:
