@@ -967,7 +967,7 @@ int pcas_autotune(const void* f0, const void* mean, const void* U, int dtype, in
         }
         return PCAS_OK;
     };
-    // 0. empty-space skipping, judged by the warps (which mark the bricks) and
+    // 0. empty-space skipping, timed over the warps (which mark the bricks) and
     //    the projectors (which walk them)
     {
         const int onoff[2] = {1, 0};
@@ -977,7 +977,7 @@ int pcas_autotune(const void* f0, const void* mean, const void* U, int dtype, in
         best.skip = c;
         for (int b = 0; b < NBIN; b++) ok_bin[b] = true;
     }
-    // 1. per angle bin, the layout of the solver volumes, judged by every warp
+    // 1. per angle bin, the layout of the solver volumes, timed over every warp
     //    and projector kernel together (they write and read the same buffers)
     for (int b = 0; b < NBIN && rc == PCAS_OK; b++) {
         double tt[2] = {0, 0};

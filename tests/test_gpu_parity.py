@@ -9,7 +9,7 @@ Tolerances (float32 GPU path against float64 oracle):
   warp           max |df| <= 5e-5 * max |f0|  (FP32 position i + x/s carries
                  up to ~1.5e-5 voxel of rounding for i < 256, times a jump of
                  at most max|f0| per voxel, plus margin)
-  P^T            max |dg| <= 1e-4 * max |g_oracle| (same rounding budget as P)
+  P^T            max |dg| <= 1e-4 * max |g_oracle| (same rounding allowance as P)
   J, (a, b)      relative 1e-4 / 1e-5 (FP32 sums of positive terms; FP64 across blocks)
 """
 import math
