@@ -544,7 +544,7 @@ def run_reference(args, ws_, rank):
             "data": "synthetic, same workload as our arm", "config": {"workload": workload_name(args)},
             "cpu_baseline": {"value": round(value, 5), "unit": "projections/s", "cores": os.cpu_count(),
                              "kind": "oracle",
-                             "sample": f"{done} projections of the workload, full solves, at most about 150 s of solving"},
+                             "sample": f"{done} projection{'s' if done != 1 else ''} of the workload, full solves, at most about 150 s of solving"},
             "e2e": {"value": round(value, 5), "unit": "projections/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
