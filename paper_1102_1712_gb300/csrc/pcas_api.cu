@@ -344,8 +344,17 @@ int gather_blocks(const Tune& T) {
 }
 
 // ------------------------------------------------------------ small kernels
+// Sum over lanes 0..7 (the other lanes hold zeros), returned to every lane:
+// the value of a sum over the warp, without its two levels that add zeros.
+__device__ __forceinline__ double tap_sum8(double v) {
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return __shfl_sync(0xffffffffu, v, 0);
+}
+
 // Sec. II.A fixed point c = c_ref - x(c) for the tumour centroid, by one warp:
-// lanes 0..7 own the eight taps of the trilinear DVF sample (Eq. 1 at w).
+// lanes 0..7 own the eight taps of the trilinear DVF sample (Eq. 1 at w), each
+// loading its tap's model values only when the iterate moves to another cell.
 // Lane 0 writes out[0..2] = c and out[3] = 1 if it converged (else 0).
 template <typename T>
 __device__ void localize_warp(const T* __restrict__ mean, const T* __restrict__ U, int K, const Grid& g,
@@ -356,12 +365,16 @@ __device__ void localize_warp(const T* __restrict__ mean, const T* __restrict__ 
     const long N = (long)g.nx * g.ny * g.nz;
     double y[3] = {0.0, 0.0, 0.0};
     int converged = 0, it = 0;
+    // mean + U w at this lane's tap voxel, kept while the iterates stay in one
+    // cell (the same values, computed once instead of once per iteration)
+    long vhold = -1;
+    double xv[3] = {0.0, 0.0, 0.0};
     for (; it < max_iter; it++) {
         double q[3] = {(cx + y[0] - ox) * isx, (cy + y[1] - oy) * isy, (cz + y[2] - oz) * isz};
         double x[3] = {0.0, 0.0, 0.0};
         if (lane < 8) {
             bool inside = true;
-            double wt = 1.0;
+            double f[3];
             long idx[3];
             const int n[3] = {g.nx, g.ny, g.nz};
             for (int c = 0; c < 3; c++) {
@@ -370,22 +383,27 @@ __device__ void localize_warp(const T* __restrict__ mean, const T* __restrict__ 
                 int bit = (lane >> c) & 1;
                 double z = qc - fl;
                 long l = (long)fl + bit;
-                wt *= bit ? z : 1.0 - z;
+                f[c] = bit ? z : 1.0 - z;
                 inside = inside && l >= 0 && l < n[c];
                 idx[c] = l;
             }
+            const double wt = (f[0] * f[1]) * f[2];
             if (inside && wt != 0.0) {
                 long v = (idx[2] * g.ny + idx[1]) * g.nx + idx[0];
-                for (int c = 0; c < 3; c++) {
-                    double val = mean ? (double)ldg_f(mean + c * N + v) : 0.0;
-                    for (int k = 0; k < K; k++) val += w[k] * (double)ldg_f(U + ((long)k * 3 + c) * N + v);
-                    x[c] = wt * val;
+                if (v != vhold) {
+                    for (int c = 0; c < 3; c++) {
+                        double val = mean ? (double)ldg_f(mean + c * N + v) : 0.0;
+                        for (int k = 0; k < K; k++) val += w[k] * (double)ldg_f(U + ((long)k * 3 + c) * N + v);
+                        xv[c] = val;
+                    }
+                    vhold = v;
                 }
+                for (int c = 0; c < 3; c++) x[c] = wt * xv[c];
             }
         }
         double change = 0.0;
         for (int c = 0; c < 3; c++) {
-            double s = warp_sum_d(x[c]);
+            double s = tap_sum8(x[c]);
             double yn = -s;
             change = fmax(change, fabs(yn - y[c]));
             y[c] = yn;
