@@ -231,9 +231,11 @@ int pcas_solver_solve(pcas_solver solver, const float* y, double angle_rad, doub
 int pcas_solver_destroy(pcas_solver solver);
 
 /* Runs of consecutive projections on one solver (a breathing sequence): the
- * warm start of Eq. (3) and the tumour localisation of Sec. II.A run inside
- * the graph, from the solutions the run keeps on the device, so projections
- * can be queued back to back with no host round trip in between.
+ * warm start of Eq. (3) runs inside the graph, from the solutions the run
+ * keeps on the device, and the tumour localisation of Sec. II.A follows each
+ * solve on a stream the solver owns (ordered after the solve by an event; the
+ * next projection's solve does not wait for it), so projections can be
+ * queued back to back with no host round trip in between.
  * pcas_solver_seq_begin: starts a run.  lp_coef: host K x L (c[k][l] as
  *   lp_fit, 1 <= L <= 8); c_ref: tumour centroid in the reference CT (mm);
  *   loc_max_iter, loc_tol_mm: as localize_tumor; w_hist: host n_hist x K

@@ -1264,8 +1264,9 @@ int lp_predict(const double* hist, const double* c, int K, int L, double* w0) {
 // instantiated graph serves every gantry angle, and launches can be queued
 // ahead.  In a run of consecutive projections (pcas_solver_seq_*) the warm
 // start of Eq. (3) is taken on the device from the solutions kept there, and
-// the graph ends with the tumour localisation of Sec. II.A: projection after
-// projection goes by without a host round trip.
+// the tumour localisation of Sec. II.A follows each solve on a stream of its
+// own (it overlaps the next projection's solve, which does not need it):
+// projection after projection goes by without a host round trip.
 // ===========================================================================
 namespace {
 
@@ -1274,6 +1275,7 @@ struct InitBlock {
     double mu0, alpha, beta, mu_min;
     int K, max_trials, max_iter;
     int seq;                  // 1: start from the run's history (Eq. 3), localise at the end
+    int slot;                 // ring slot of this launch (a run's result record)
 };
 
 // Per-launch staging (view + start), one device copy and SEQ_RING host slots.
@@ -1296,7 +1298,8 @@ struct SeqBlock {
     double hist[LP_MAX][PCAS_KMAX];
 };
 
-// Result of one projection of a run, copied to a host slot after the launch.
+// Result of one projection of a run (a ring of SEQ_RING on the device, one per
+// slot), copied to the host slot after the localisation.
 struct SeqOut {
     double w[PCAS_KMAX];
     double c[4];                      // centroid (mm) and 1 if the fixed point converged
@@ -1363,29 +1366,38 @@ __global__ void k_ctrl_iter_end(SolveState* st, cudaGraphConditionalHandle h_out
 // End of a device-driven solve (one warp).  In a run: the tumour centroid at
 // the solution (Sec. II.A, the same fixed point as localize_tumor), the
 // solution pushed onto the history, and the result record.
-template <typename T>
-__global__ void k_seq_end(SolveState* st, const InitBlock* __restrict__ ib, SeqBlock* sq, SeqOut* out,
-                          const T* __restrict__ mean, const T* __restrict__ U, int K, Grid g) {
+__global__ void k_seq_end(SolveState* st, const InitBlock* __restrict__ ib, SeqBlock* sq, SeqOut* out_ring) {
+    if (threadIdx.x != 0) return;
     if (!ib->seq) {
-        if (threadIdx.x == 0) st->launches += 1;
+        st->launches += 1;
         return;
     }
     double w[PCAS_KMAX];
     for (int k = 0; k < PCAS_KMAX; k++) w[k] = st->w[k];
-    double c[4];
-    localize_warp(mean, U, K, g, w, sq->o[0], sq->o[1], sq->o[2], sq->is[0], sq->is[1], sq->is[2],
-                  sq->c_ref[0], sq->c_ref[1], sq->c_ref[2], sq->loc_max_iter, sq->loc_tol, c);
-    if (threadIdx.x != 0) return;
     for (int l = LP_MAX - 1; l > 0; l--)
         for (int k = 0; k < PCAS_KMAX; k++) sq->hist[l][k] = sq->hist[l - 1][k];
     for (int k = 0; k < PCAS_KMAX; k++) sq->hist[0][k] = w[k];
     if (sq->n < LP_MAX) sq->n += 1;
     sq->f0_ready = 1;
     st->launches += 1;
+    SeqOut* out = out_ring + ib->slot;
     for (int k = 0; k < PCAS_KMAX; k++) out->w[k] = w[k];
-    for (int i = 0; i < 4; i++) out->c[i] = c[i];
     out->J0 = st->J0; out->J = st->J; out->a = st->a; out->b = st->b; out->mu = st->mu;
     out->iters = st->iters; out->evals = st->evals; out->phase = st->phase; out->launches = st->launches;
+}
+
+// The tumour centroid at a run's solution (Sec. II.A, the same fixed point as
+// localize_tumor), into the projection's result record.  Launched after the
+// solve on the solver's localisation stream; reads only the run's constant
+// parameters and the record's own coefficients.
+template <typename T>
+__global__ void k_seq_loc(const SeqBlock* __restrict__ sq, SeqOut* out, const T* __restrict__ mean,
+                          const T* __restrict__ U, int K, Grid g) {
+    double w[PCAS_KMAX];
+    for (int k = 0; k < PCAS_KMAX; k++) w[k] = out->w[k];
+    localize_warp(mean, U, K, g, w, sq->o[0], sq->o[1], sq->o[2], sq->is[0], sq->is[1], sq->is[2],
+                  sq->c_ref[0], sq->c_ref[1], sq->c_ref[2], sq->loc_max_iter, sq->loc_tol, out->c);
+    if (threadIdx.x == 0) out->launches += 1;
 }
 
 #define PCAS_G(call)                                                                              \
@@ -1430,11 +1442,13 @@ struct pcas_solver_s {
     float* y;             // device, M floats (in the workspace)
     Stage* d_stage;       // device (in the workspace): view + start of the next launch
     SeqBlock* d_seq;      // device: the run of consecutive projections
-    SeqOut* d_out;        // device: result of the last projection of a run
+    SeqOut* d_out;        // device [SEQ_RING]: results of a run, by slot
     Stage* h_ring;        // pinned host [SEQ_RING]: staging per launch
     SeqOut* h_out;        // pinned host [SEQ_RING]: results of a run
     SeqBlock* h_seq;      // pinned host: run parameters on their way to the device
     cudaEvent_t ev[SEQ_RING];   // a slot is free again once its launch passed this
+    cudaEvent_t ev_solved[SEQ_RING];  // a run's solve of the slot is done (localisation may start)
+    cudaStream_t loc_stream;          // localisations of a run's projections
     long long next;       // tickets handed out (slot = ticket % SEQ_RING)
     long long seq_first;  // first ticket of the current run (-1: no run)
     long long slot_ticket[SEQ_RING];  // ticket of a run's projection in each slot (-1: none)
@@ -1458,7 +1472,7 @@ namespace {
 
 size_t solver_extra(const pcas_cb* cb) {
     return align256((size_t)cb->nu * cb->nv * sizeof(float)) + align256(sizeof(Stage)) + align256(sizeof(SeqBlock)) +
-           align256(sizeof(SeqOut));
+           align256(SEQ_RING * sizeof(SeqOut));
 }
 
 // Captures one device-driven solve into `graph` as an independent branch
@@ -1510,23 +1524,7 @@ int capture_solve(pcas_solver s, cudaGraph_t graph, cudaStream_t cs, const float
     PCAS_G(cudaGetLastError());
     cudaGraph_t outer_body;
     PCAS_TRY(add_while(cs, s->h_outer, &outer_body));
-    switch (s->dtype) {
-        case DT_F32:
-            k_seq_end<float><<<1, 32, 0, cs>>>(W.st, &s->d_stage->ib, s->d_seq, s->d_out,
-                                               static_cast<const float*>(s->mean),
-                                               static_cast<const float*>(s->U), s->K, g);
-            break;
-        case DT_BF16:
-            k_seq_end<__nv_bfloat16><<<1, 32, 0, cs>>>(W.st, &s->d_stage->ib, s->d_seq, s->d_out,
-                                                       static_cast<const __nv_bfloat16*>(s->mean),
-                                                       static_cast<const __nv_bfloat16*>(s->U), s->K, g);
-            break;
-        default:
-            k_seq_end<__half><<<1, 32, 0, cs>>>(W.st, &s->d_stage->ib, s->d_seq, s->d_out,
-                                                static_cast<const __half*>(s->mean),
-                                                static_cast<const __half*>(s->U), s->K, g);
-            break;
-    }
+    k_seq_end<<<1, 32, 0, cs>>>(W.st, &s->d_stage->ib, s->d_seq, s->d_out);
     PCAS_G(cudaGetLastError());
     cudaGraph_t done;
     PCAS_G(cudaStreamEndCapture(cs, &done));
@@ -1596,6 +1594,7 @@ int solver_stage(pcas_solver s, double angle_rad, double off_u, double off_v, co
     ib.mu0 = s->prm.mu0; ib.alpha = s->prm.alpha; ib.beta = s->prm.beta; ib.mu_min = s->prm.mu_min;
     ib.K = s->K; ib.max_trials = s->prm.max_trials; ib.max_iter = s->prm.max_iter;
     ib.seq = seq;
+    ib.slot = slot;
     h.ib = ib;
     PCAS_CUDA(cudaMemcpyAsync(s->d_stage, &h, sizeof(Stage), cudaMemcpyHostToDevice, st));
     if (slot_out) *slot_out = slot;
@@ -1624,8 +1623,14 @@ void solver_free(pcas_solver s) {
     if (!s) return;
     if (s->exec) cudaGraphExecDestroy(s->exec);
     if (s->graph) cudaGraphDestroy(s->graph);
-    for (int i = 0; i < SEQ_RING; i++)
+    if (s->loc_stream) {
+        cudaStreamSynchronize(s->loc_stream);
+        cudaStreamDestroy(s->loc_stream);
+    }
+    for (int i = 0; i < SEQ_RING; i++) {
         if (s->ev[i]) cudaEventDestroy(s->ev[i]);
+        if (s->ev_solved[i]) cudaEventDestroy(s->ev_solved[i]);
+    }
     if (s->h_ring) cudaFreeHost(s->h_ring);
     if (s->h_out) cudaFreeHost(s->h_out);
     if (s->h_seq) cudaFreeHost(s->h_seq);
@@ -1686,8 +1691,11 @@ int pcas_solver_create(pcas_solver* out, const void* f0, const void* mean, const
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&s->h_out, SEQ_RING * sizeof(SeqOut), cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&s->h_seq, sizeof(SeqBlock), cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&s->h_state, sizeof(SolveState), cudaHostAllocDefault);
-    for (int i = 0; i < SEQ_RING && e == cudaSuccess; i++)
+    for (int i = 0; i < SEQ_RING && e == cudaSuccess; i++) {
         e = cudaEventCreateWithFlags(&s->ev[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_solved[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->loc_stream, cudaStreamNonBlocking);
     // zero the halos once: the warp kernels never write them
     if (e == cudaSuccess) e = cudaMemsetAsync(s->W.fpad, 0, s->W.fpad_bytes + s->W.fpad4_bytes, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->W.f0h, 0, s->W.f0h_bytes, st);
@@ -1749,6 +1757,7 @@ int pcas_solver_seq_begin(pcas_solver s, const double* lp_coef, int L, const dou
     if (n_hist > 0) PCAS_TRY(check_finite(w_hist, s->K * n_hist, "w_hist"));
     cudaStream_t st = as_stream(stream);
     PCAS_CUDA(cudaStreamSynchronize(st));           // the previous run's copy of h_seq is done
+    PCAS_CUDA(cudaStreamSynchronize(s->loc_stream));   // and its localisations (they read d_seq)
     SeqBlock& h = *s->h_seq;
     memset(&h, 0, sizeof(SeqBlock));
     for (int k = 0; k < s->K; k++)
@@ -1779,8 +1788,30 @@ int pcas_solver_seq_enqueue(pcas_solver s, const void* y, double angle_rad, cons
     const size_t M = (size_t)s->cb.nu * s->cb.nv;
     if (y && y != s->y) PCAS_CUDA(cudaMemcpyAsync(s->y, y, M * sizeof(float), cudaMemcpyDefault, st));
     PCAS_CUDA(cudaGraphLaunch(s->exec, st));
-    PCAS_CUDA(cudaMemcpyAsync(&s->h_out[slot], s->d_out, sizeof(SeqOut), cudaMemcpyDeviceToHost, st));
-    PCAS_CUDA(cudaEventRecord(s->ev[slot], st));
+    // the localisation and the result record on the solver's own stream, so
+    // that the next projection's solve does not wait for them
+    cudaStream_t ls = s->loc_stream;
+    PCAS_CUDA(cudaEventRecord(s->ev_solved[slot], st));
+    PCAS_CUDA(cudaStreamWaitEvent(ls, s->ev_solved[slot], 0));
+    const Grid g = make_grid(&s->vol);
+    SeqOut* d_res = s->d_out + slot;
+    switch (s->dtype) {
+        case DT_F32:
+            k_seq_loc<float><<<1, 32, 0, ls>>>(s->d_seq, d_res, static_cast<const float*>(s->mean),
+                                               static_cast<const float*>(s->U), s->K, g);
+            break;
+        case DT_BF16:
+            k_seq_loc<__nv_bfloat16><<<1, 32, 0, ls>>>(s->d_seq, d_res, static_cast<const __nv_bfloat16*>(s->mean),
+                                                       static_cast<const __nv_bfloat16*>(s->U), s->K, g);
+            break;
+        default:
+            k_seq_loc<__half><<<1, 32, 0, ls>>>(s->d_seq, d_res, static_cast<const __half*>(s->mean),
+                                                static_cast<const __half*>(s->U), s->K, g);
+            break;
+    }
+    PCAS_CUDA(cudaGetLastError());
+    PCAS_CUDA(cudaMemcpyAsync(&s->h_out[slot], d_res, sizeof(SeqOut), cudaMemcpyDeviceToHost, ls));
+    PCAS_CUDA(cudaEventRecord(s->ev[slot], ls));
     s->slot_ticket[slot] = s->next - 1;
     s->slot_counted[slot] = false;
     *ticket = s->next - 1;
