@@ -206,8 +206,9 @@ int localize_tumor(const float* mean, const float* U, int K, const double* w,
  *   the workspace (pcas_solver_workspace_bytes, device, 256-byte aligned) are
  *   owned by the caller and must stay valid until destroy; cb gives the
  *   detector shape (its angle and offsets are per-solve); params are fixed.
- *   Allocates pinned host staging buffers and builds the graph; not for
- *   use inside stream capture.
+ *   Allocates pinned host staging buffers, a stream for the localisations
+ *   of runs, and builds the graph; not for use inside stream capture.
+ *   pcas_solver_destroy waits for that stream before it frees them.
  * pcas_solver_solve: y (device, [nv][nu]) is copied into the solver's image
  *   buffer unless it is that buffer (pcas_solver_y_buffer) or NULL; the view
  *   is the creation view with this angle and these detector offsets.
