@@ -962,9 +962,16 @@ int pcas_autotune(const void* f0, const void* mean, const void* U, int dtype, in
     bool ok_bin[NBIN];
     for (int b = 0; b < NBIN; b++) ok_bin[b] = true;
     const int probe[4] = {0, 2, 4, 6};
+    // A shape replaces the one in place (the default, or the choice of an
+    // earlier step) only when it is faster by more than this margin: choices
+    // that timing noise would flip from run to run -- and with them, through
+    // the order of the projectors' and the gradient's sums, the rounding of
+    // the results -- stay put.
+    const double keep = 0.985;
     auto sweep = [&](auto apply, const int* cands, int ncand, const int* kinds, int nkinds, const int* bins,
                      int nbins, int* choice) -> int {
-        double bestt = 0.0;
+        double bestt = 0.0, inct = -1.0;
+        const int inc = *choice;
         for (int c = 0; c < ncand; c++) {
             Tune X = best;
             apply(X, cands[c]);
@@ -978,11 +985,13 @@ int pcas_autotune(const void* f0, const void* mean, const void* U, int dtype, in
                 for (int k = 0; k < nkinds; k++) t += a[kinds[k]];
                 used++;
             }
+            if (used && cands[c] == inc) inct = t;
             if (used && (c == 0 || t < bestt)) {
                 bestt = t;
                 *choice = cands[c];
             }
         }
+        if (inct > 0.0 && *choice != inc && bestt > keep * inct) *choice = inc;
         return PCAS_OK;
     };
     // 0. empty-space skipping, timed over the warps (which mark the bricks) and
@@ -1008,13 +1017,15 @@ int pcas_autotune(const void* f0, const void* mean, const void* U, int dtype, in
             tt[sw] = a[PCAS_K_WARP_PCA] + a[PCAS_K_DRR_SOLVER] + 2.0 * (a[PCAS_K_WARP_BATCH] + a[PCAS_K_DRR_BATCH]);
         }
         if (rc != PCAS_OK || !ok_bin[b]) continue;
-        best.swap[b] = tt[1] < tt[0] ? 1 : 0;
+        const int cur = best.swap[b] ? 1 : 0;
+        if (tt[1 - cur] < keep * tt[cur]) best.swap[b] = (unsigned char)(1 - cur);
     }
     // 2. per angle bin, the patch width and chunk of the batch projector
     for (int b = 0; b < NBIN && rc == PCAS_OK; b++) {
         if (!ok_bin[b]) continue;
-        double bestt = 0.0;
-        int blw = best.lw4[b], bch = best.chunk4[b];
+        double bestt = 0.0, inct = -1.0;
+        const int ilw = best.lw4[b], ich = best.chunk4[b];
+        int blw = ilw, bch = ich;
         bool first = true;
         for (int lw = 2; lw <= 4 && rc == PCAS_OK; lw++) {
             const int chunks[3] = {12, 16, 24};
@@ -1024,6 +1035,7 @@ int pcas_autotune(const void* f0, const void* mean, const void* U, int dtype, in
                 X.chunk4[b] = (unsigned char)chunks[c];
                 rc = tr.run(X, b, a);
                 if (rc != PCAS_OK || a[PCAS_K_DRR_BATCH] <= 0.0) continue;
+                if (lw == ilw && chunks[c] == ich) inct = a[PCAS_K_DRR_BATCH];
                 if (first || a[PCAS_K_DRR_BATCH] < bestt) {
                     bestt = a[PCAS_K_DRR_BATCH];
                     blw = lw;
@@ -1032,6 +1044,7 @@ int pcas_autotune(const void* f0, const void* mean, const void* U, int dtype, in
                 }
             }
         }
+        if (inct > 0.0 && bestt > keep * inct) { blw = ilw; bch = ich; }
         best.lw4[b] = (unsigned char)blw;
         best.chunk4[b] = (unsigned char)bch;
     }
@@ -1056,7 +1069,7 @@ int pcas_autotune(const void* f0, const void* mean, const void* U, int dtype, in
         const int ka[1] = {PCAS_K_ADJ_GRAD};
         const int bins2[2] = {0, 4};
         int c = best.vt;
-        rc = sweep([](Tune& X, int v) { X.vt = v; }, vts, NVOXTILE, ka, 1, bins2, 2, &c);
+        rc = sweep([](Tune& X, int v) { X.vt = v; }, vts, NVOXTILE, ka, 1, probe, 4, &c);
         best.vt = c;
         int g = best.adj_mult;
         if (rc == PCAS_OK) rc = sweep([](Tune& X, int v) { X.adj_mult = v; }, gs, 3, ka, 1, bins2, 2, &g);
