@@ -10,7 +10,7 @@ module only compiles it with gcc and marshals numpy arrays through ctypes.
 Parity status of each routine (what pins it is in ``tests/test_oracle_*.py``):
   pca_dvf, warp_volume, trilinear, trilinear_grad, drr_forward, drr_ray,
   siddon_forward, siddon_ray, drr_adjoint, intensity_fit, cost, cost_grad, grad_forward_mode,
-  warp_adjoint, cost_grad_f0, solve_projection, localize_tumor, lp_fit,
+  warp_adjoint, cost_grad_f0, solve_projection, solve_projection_log, localize_tumor, lp_fit,
   lp_predict -- all pinned.
 """
 from __future__ import annotations
@@ -96,6 +96,9 @@ def lib():
                                                   C.c_double, C.c_int, _D, _D, _D]),
                 ("oracle_solve_projection", C.c_int, [_D, _D, _D, C.c_int, _D, C.POINTER(Vol), C.POINTER(CB),
                                                       _D, C.POINTER(Params), _D, C.POINTER(Stats), _D]),
+                ("oracle_solve_projection_log", C.c_int, [_D, _D, _D, C.c_int, _D, C.POINTER(Vol),
+                                                          C.POINTER(CB), _D, C.POINTER(Params), _D,
+                                                          C.POINTER(Stats), _D, _D]),
                 ("oracle_localize_tumor", C.c_int, [_D, _D, C.c_int, _D, C.POINTER(Vol), _D, C.c_int,
                                                     C.c_double, _D]),
                 ("oracle_lp_fit", C.c_int, [_D, C.c_int, C.c_int, C.c_int, _D]),
@@ -292,6 +295,38 @@ def solve_projection(f0, mean, U, y, vol, cb, w_init, params: dict):
     _check(rc, "solve_projection")
     stats = {k: getattr(st, k) for k, _ in Stats._fields_}
     return w_out, stats, trace[: stats["iters"] + 1]
+
+
+def solve_projection_log(f0, mean, U, y, vol, cb, w_init, params: dict):
+    """solve_projection with a record of every iteration that reached the line
+    search: a list of dicts with J, a, b (at the iterate, after Eq. A.1), gnorm,
+    mu (the accepted step size, 0.0 if none), trials, accepted, and the
+    iterate w, gradient G and direction d."""
+    N = _nvox(vol)
+    f0 = _d(f0).ravel()
+    U = _d(U).reshape(-1, 3, N)
+    K = U.shape[0]
+    mean = None if mean is None else _d(mean).reshape(3, N)
+    y, w0 = _d(y).ravel(), _d(w_init)
+    prm = Params(params["mu0"], params["alpha"], params["beta"], params["mu_min"],
+                 params["max_iter"], params["max_trials"], params["step"])
+    w_out = np.zeros(K)
+    st = Stats()
+    trace = np.full(params["max_iter"] + 1, np.nan)
+    stride = 7 + 3 * K
+    log = np.full((max(params["max_iter"], 1), stride), np.nan)
+    rc = lib().oracle_solve_projection_log(_p(f0), _p(mean), _p(U), K, _p(y), C.byref(vol_struct(vol)),
+                                           C.byref(cb_struct(cb)), _p(w0), C.byref(prm), _p(w_out),
+                                           C.byref(st), _p(trace), _p(log))
+    _check(rc, "solve_projection_log")
+    stats = {k: getattr(st, k) for k, _ in Stats._fields_}
+    rows = []
+    for r in log:
+        if np.isnan(r[0]):
+            break
+        rows.append(dict(J=r[0], a=r[1], b=r[2], gnorm=r[3], mu=r[4], trials=int(r[5]), accepted=bool(r[6]),
+                         w=r[7:7 + K].copy(), G=r[7 + K:7 + 2 * K].copy(), d=r[7 + 2 * K:7 + 3 * K].copy()))
+    return w_out, stats, rows
 
 
 def localize_tumor(mean, U, w, vol, c_ref, max_iter=50, tol_mm=1e-6):

@@ -485,10 +485,10 @@ int oracle_cost_grad_f0(const double* f0, const double* mean, const double* U, i
  * first mu with J(w + mu d) <= J(w) - alpha mu ||G||, else mu <- beta mu.  When
  * mu drops below mu_min (or the trial cap is reached) no step is taken and the
  * solve stops; it also stops after max_iter iterations or when ||G|| = 0. */
-int oracle_solve_projection(const double* f0, const double* mean, const double* U, int K,
-                            const double* y, const ovol* vol, const ocb* cb,
-                            const double* w_init, const oparams* prm, double* w_out,
-                            ostats* st, double* J_trace) {
+int oracle_solve_projection_log(const double* f0, const double* mean, const double* U, int K,
+                                const double* y, const ovol* vol, const ocb* cb,
+                                const double* w_init, const oparams* prm, double* w_out,
+                                ostats* st, double* J_trace, double* it_log) {
     if (!vol_ok(vol) || !prm || !cb_ok(vol, cb, prm->step) || K < 1 || K > 64 || !w_init ||
         !w_out || !st)
         return 1;
@@ -513,6 +513,9 @@ int oracle_solve_projection(const double* f0, const double* mean, const double* 
         J = oracle_cost(p, y, M, a, b);
         if (it == 0) st->J0 = J;
         if (J_trace) J_trace[it] = J;
+        const double Jw = J;
+        double wlog[64];
+        for (int k = 0; k < K; k++) wlog[k] = w[k];
         /* gradient at w with (a, b) fixed; dvf/f currently hold w's fields */
         rc = oracle_pca_dvf(mean, U, K, w, vol, dvf);
         for (long i = 0; i < M; i++) r[i] = p[i] - a * y[i] - b;
@@ -524,9 +527,10 @@ int oracle_solve_projection(const double* f0, const double* mean, const double* 
         gn = sqrt(gn);
         if (gn == 0.0) break;
         for (int k = 0; k < K; k++) d[k] = -G[k] / gn;
-        int accepted = 0;
+        int accepted = 0, tried = 0;
         mu = prm->mu0;                                            /* step 2, (A.2) */
         for (int tr = 0; tr < prm->max_trials && mu >= prm->mu_min; tr++) {
+            tried++;
             for (int k = 0; k < K; k++) wt[k] = w[k] + mu * d[k];
             rc = render(f0, mean, U, K, wt, vol, cb, step, dvf, f, pt);
             st->evals++;
@@ -542,6 +546,16 @@ int oracle_solve_projection(const double* f0, const double* mean, const double* 
             mu *= prm->beta;
         }
         if (rc) break;
+        if (it_log) {
+            double* row = it_log + (long)it * ORACLE_LOG_STRIDE(K);
+            row[0] = Jw; row[1] = a; row[2] = b; row[3] = gn;
+            row[4] = accepted ? mu : 0.0; row[5] = tried; row[6] = accepted;
+            for (int k = 0; k < K; k++) {
+                row[7 + k] = wlog[k];
+                row[7 + K + k] = G[k];
+                row[7 + 2 * K + k] = d[k];
+            }
+        }
         st->iters++;
         if (J_trace) J_trace[it + 1] = J;
         if (!accepted) break;
@@ -550,6 +564,13 @@ int oracle_solve_projection(const double* f0, const double* mean, const double* 
     for (int k = 0; k < K; k++) w_out[k] = w[k];
     free(dvf); free(f); free(g); free(p); free(pt); free(r);
     return rc;
+}
+
+int oracle_solve_projection(const double* f0, const double* mean, const double* U, int K,
+                            const double* y, const ovol* vol, const ocb* cb,
+                            const double* w_init, const oparams* prm, double* w_out,
+                            ostats* st, double* J_trace) {
+    return oracle_solve_projection_log(f0, mean, U, K, y, vol, cb, w_init, prm, w_out, st, J_trace, NULL);
 }
 
 /* ------------------------------------------------- Sec. II.A: localisation

@@ -107,6 +107,16 @@ int oracle_solve_projection(const double* f0, const double* mean, const double* 
                             const double* y, const ovol* vol, const ocb* cb,
                             const double* w_init, const oparams* prm, double* w_out,
                             ostats* st, double* J_trace);
+/* The same solve, also recording each iteration that reaches the line search
+ * (||G|| > 0; row it of it_log, ORACLE_LOG_STRIDE(K) doubles; rows not reached are left
+ * as the caller set them): J, a, b at the iterate (after Eq. A.1), ||G||, the
+ * accepted step size (0 if none), the trials tried in the iteration, 1 if a
+ * step was accepted (else 0), then the iterate w (K), G (K) and d (K). */
+#define ORACLE_LOG_STRIDE(K) (7 + 3 * (K))
+int oracle_solve_projection_log(const double* f0, const double* mean, const double* U, int K,
+                                const double* y, const ovol* vol, const ocb* cb,
+                                const double* w_init, const oparams* prm, double* w_out,
+                                ostats* st, double* J_trace, double* it_log);
 /* Sec. II.A: solve c + x(c) = c_ref by y <- -x(c_ref + y). */
 int oracle_localize_tumor(const double* mean, const double* U, int K, const double* w,
                           const ovol* vol, const double c_ref[3], int max_iter,
