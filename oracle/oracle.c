@@ -3,7 +3,10 @@
  *
  * Slow and literal on purpose: each function is the paper's definition
  * written out, so it can be checked against the text by eye.  It shares no
- * code with the CUDA path.
+ * code with the CUDA path.  OpenMP splits only loops whose iterations share no
+ * sum (rays of the forward projectors, voxels of the DVF, the warp and the
+ * forward-mode Jacobian), so no result depends on the thread count; the P^T
+ * scatter and every reduction run serially in their written order.
  */
 #include "oracle.h"
 
@@ -22,7 +25,9 @@ int oracle_pca_dvf(const double* mean, const double* U, int K, const double* w,
                    const ovol* vol, double* dvf) {
     if (!vol_ok(vol) || K < 0 || (K > 0 && (!U || !w)) || !dvf) return 1;
     long N = nvox(vol);
+    /* independent voxels: the threads share no sum */
     for (int c = 0; c < 3; c++) {
+#pragma omp parallel for schedule(static)
         for (long n = 0; n < N; n++) {
             double x = mean ? mean[c * N + n] : 0.0;
             for (int k = 0; k < K; k++) x += U[((long)k * 3 + c) * N + n] * w[k];
@@ -82,6 +87,8 @@ void oracle_trilinear_grad(const double* f0, const ovol* vol, double q1, double 
 int oracle_warp_volume(const double* f0, const double* dvf, const ovol* vol, double* f) {
     if (!vol_ok(vol) || !f0 || !dvf || !f) return 1;
     long N = nvox(vol);
+    /* independent voxels: the threads share no sum */
+#pragma omp parallel for schedule(static)
     for (long k = 0; k < vol->nz; k++)
         for (long j = 0; j < vol->ny; j++)
             for (long i = 0; i < vol->nx; i++) {
@@ -408,6 +415,7 @@ int oracle_grad_forward_mode(const double* f0, const double* mean, const double*
     double* ph = malloc(sizeof(double) * M);
     int st = render(f0, mean, U, K, w, vol, cb, step, dvf, f, p);
     for (int k = 0; !st && k < K; k++) {
+#pragma omp parallel for schedule(static)
         for (long kk = 0; kk < vol->nz; kk++)
             for (long j = 0; j < vol->ny; j++)
                 for (long i = 0; i < vol->nx; i++) {
