@@ -128,6 +128,97 @@ def make_inputs(irregular: bool):
     return vol, f0, c_ref, U, trace, train, angles
 
 
+def precision_inputs():
+    """The precision workload's inputs (numpy): 512x512x160 phantom at 1x1x2 mm,
+    K = 5 eigenvector fields smoothed on a coarse grid, the irregular trace, the
+    training trace of the predictor and the gantry angles."""
+    from paper_1102_1712_gb300 import synth as S
+    W = PRECISION
+    vol = S.volume(*W["vol"])
+    f0, c_ref = S.phantom(vol, W["tumor_mm"], seed=W["seeds"]["phantom"])
+    U = S.eigen_dvfs(vol, W["K"], seed=W["seeds"]["dvf"], coarse=(2, 4, 4))
+    trace = S.breathing_trace(W["n_proj"], W["fps"], W["period_s"], W["amp_mm"], K=W["K"], irregular=True,
+                              drift_mm=W["drift_mm"], jitter=W["jitter"], amp_jitter=W["amp_jitter"],
+                              seed=W["seeds"]["trace"])
+    train = S.breathing_trace(400, W["fps"], W["period_s"], W["amp_mm"], K=W["K"], t0=0.37)
+    angles = S.gantry_angles(W["n_proj"], 360.0)
+    return vol, f0, c_ref, U, trace, train, angles
+
+
+def batch_inputs():
+    """The batch workload's 64 problems (numpy): volume, K, view, phantom,
+    eigenvector fields (one array per (size, K) model, shared), tumour centre,
+    planted w and ray-march step."""
+    from paper_1102_1712_gb300 import synth as S
+    W = BATCH
+    g = S.rng(99)
+    models = {}
+    probs = []
+    for i in range(W["n"]):
+        nx, ny, nz = W["sizes"][i % 3]
+        K = W["Ks"][i % 2]
+        nu, nv = W["dets"][i % 4]
+        vol = S.volume(nx, ny, nz, W["fov"][0] / nx, W["fov"][0] / ny, W["fov"][1] / nz)
+        key = (i % 3, K)
+        if key not in models:
+            coarse = (1, 1, 1) if nx <= 128 else (2, 2, 2)
+            models[key] = S.eigen_dvfs(vol, K, seed=200 + 10 * (i % 3) + K, coarse=coarse)
+        f0, c_ref = S.phantom(vol, 15.0, seed=100 + i)
+        cb = S.cone_beam(nu, nv, 400.0 / nu, 400.0 / nu, float(g.uniform(0, 2 * np.pi)))
+        w_true = g.standard_normal(K)
+        probs.append(dict(vol=vol, K=K, cb=cb, f0=f0, U=models[key], model=key, c_ref=c_ref, w_true=w_true,
+                          step=0.5 * min(vol["sx"], vol["sy"], vol["sz"])))
+    return probs
+
+
+def batch_fingerprint_parts(probs):
+    """What input_fingerprint hashes for the batch workload: the planted w and
+    tumour centres of the 64 problems, and samples of every model and phantom."""
+    seen, parts = set(), []
+    for pb in probs:
+        if pb["model"] not in seen:
+            seen.add(pb["model"])
+            parts.append(np.asarray(pb["U"]).ravel()[::97])
+        parts.append(np.asarray(pb["f0"]).ravel()[::97])
+    return (np.concatenate([pb["w_true"] for pb in probs]), np.concatenate([pb["c_ref"] for pb in probs]),
+            np.concatenate(parts))
+
+
+# Tumour centroids at the planted coefficients (the truth of mm_error), found
+# by the FP64 oracle's localisation and stored by tests/golden/make_bench_truth.py
+# with a fingerprint of the inputs they belong to.
+TRUTH_FILE = os.path.join(ROOT, "tests", "golden", "bench_truth.json")
+
+
+def input_fingerprint(trace, c_ref, U):
+    """Samples of the inputs a stored truth belongs to: every 7th row of the
+    planted trace, the tumour centre and about 200 values of the eigenvector
+    fields (inputs only: no arithmetic of the method).  Compared with a
+    relative tolerance, so that last-bit differences of another machine's
+    math library do not count as other inputs."""
+    tr = np.asarray(trace, dtype=np.float64).reshape(len(trace), -1)
+    u = np.asarray(U, dtype=np.float64).ravel()
+    return {"trace": tr[::7].ravel().tolist(), "c_ref": np.asarray(c_ref, dtype=np.float64).ravel().tolist(),
+            "U": u[:: max(1, u.size // 200)].tolist()}
+
+
+def same_inputs(a, b, rtol=1e-5):
+    return all(k in a and k in b and len(a[k]) == len(b[k]) and
+               np.allclose(a[k], b[k], rtol=rtol, atol=rtol * max(1e-12, float(np.abs(b[k]).max(initial=0.0))))
+               for k in ("trace", "c_ref", "U"))
+
+
+def truth(name, trace, c_ref, U):
+    """Stored oracle truth of workload `name` for these inputs, (T, 3) mm."""
+    try:
+        rec = json.load(open(TRUTH_FILE))[name]
+    except (OSError, KeyError, ValueError) as e:
+        raise SystemExit(f"no stored truth for {name} ({e}): run tests/golden/make_bench_truth.py")
+    if not same_inputs(input_fingerprint(trace, c_ref, U), rec["fingerprint"]):
+        raise SystemExit(f"stored truth for {name} belongs to other inputs: run tests/golden/make_bench_truth.py")
+    return np.asarray(rec["c_true"], dtype=np.float64)
+
+
 def view(angle):
     from paper_1102_1712_gb300 import synth as S
     d = WORKLOAD["det"]
@@ -284,7 +375,7 @@ def run_ours(args, ws_, rank, local):
     # measured projections: the planted volume f(w_true(t)) rendered by Siddon's
     # projector (or the solver's own) in the library + seeded noise
     ys = torch.empty((n_used, M), dtype=torch.float32, device=dev)
-    c_true = np.zeros((n_used, 3))
+    c_true = truth("sequence-irregular" if args.irregular else "sequence-regular", trace, c_ref, U)
     for t in range(n_used):
         f = P.warp_volume(tf0, P.pca_dvf(None, tU, trace[t], vol), vol)
         if args.projector == "siddon":
@@ -293,7 +384,6 @@ def run_ours(args, ws_, rank, local):
             p = P.drr_forward(f, vol, view(angles[t]), step)
         sigma = WORKLOAD["noise"] * float(p.abs().max())
         ys[t] = p + torch.from_numpy(S.gaussian_noise(M, sigma, seed=1000 * WORKLOAD["seeds"]["noise"] + t)).to(dev)
-        c_true[t], _ = P.localize_tumor(None, tU, trace[t], vol, c_ref)
     c_lp = P.lp_fit(train, 2)
     prm = P.default_params(step)
     wsp = P.Workspace(vol, view(0.0), K, device=dev)
@@ -392,7 +482,7 @@ def run_ours(args, ws_, rank, local):
     iters = np.array([st["iters"] for _, st, _ in timed])
     evals = np.array([st["evals"] for _, st, _ in timed])
     pk, pk_kind = peaks()
-    kb = kernel_bytes(N, M, K, False)
+    kb = kernel_bytes(N, M, K, has_mean=False)
     kernels = {}
     for name in ("warp_pca", "warp_batch", "drr_solver", "drr_batch", "resid", "adjoint_grad"):
         n, tot = prof[name]
@@ -406,9 +496,13 @@ def run_ours(args, ws_, rank, local):
     launches = launches_timed
     # the whole path in the one-at-a-time accounting of the method: per
     # projection iters gradient evaluations of B_g bytes and (evals - 1) trial
-    # evaluations of B_t bytes, over the device-driven run's time
-    B_g = (24 * (K + 1) + 12) * N + 16 * M
-    B_t = (12 * (K + 1) + 12) * N + 4 * M
+    # evaluations of B_t bytes, over the device-driven run's time; the motion
+    # model is read twice per gradient evaluation and once per trial (12 bytes
+    # per voxel and field: the K eigenvectors, and the mean only where there is one)
+    has_mean = False
+    nf = K + (1 if has_mean else 0)
+    B_g = (24 * nf + 12) * N + 16 * M
+    B_t = (12 * nf + 12) * N + 4 * M
     B_path = float(np.sum(iters * B_g + (evals - 1) * B_t))
     path_run_gbs = B_path / (ms / 1e3) / 1e9
     total_alg = sum(kernels[k]["alg_bytes"] * kernels[k]["launches"] for k in kernels)
@@ -443,10 +537,14 @@ def run_ours(args, ws_, rank, local):
                      "issue_active_frac": ncu_field(dom, "issue_active_frac", float),
                      "path_alg_gbs": round(total_alg / (ms_host / 1e3) / 1e9, 1),
                      "path_frac": round(total_alg / (ms_host / 1e3) / 1e9 / pk["hbm_gbs"], 4),
+                     "path_bytes": "the bytes the kernels move (sum over launches of each kernel's algorithmic "
+                                   "bytes), over the host-driven pass's time",
                      "run_path_gbs": round(path_run_gbs, 1),
                      "run_path_frac": round(path_run_gbs / pk["hbm_gbs"], 4),
-                     "run_path_bytes": "per projection iters * ((24(K+1)+12)N + 16M) + (evals-1) * "
-                                       "((12(K+1)+12)N + 4M), over the device-driven run's time",
+                     "run_path_bytes": "the method's one-at-a-time accounting: per projection iters * "
+                                       "((24K+12)N + 16M) + (evals-1) * ((12K+12)N + 4M) (no mean field), over "
+                                       "the device-driven run's time; the batched line search moves fewer bytes "
+                                       "than this counts",
                      "note": "kernel durations from CUDA events in the host-driven pass over the same "
                              "projections (graph launches cannot be bracketed per kernel)"},
         "host_driven": {"value": round(K_ / (ms_host / 1e3), 3), "ms_per_step": round(ms_host / K_, 4)},
@@ -561,14 +659,7 @@ def run_precision(args, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     W = PRECISION
-    vol = S.volume(*W["vol"])
-    f0, c_ref = S.phantom(vol, W["tumor_mm"], seed=W["seeds"]["phantom"])
-    U = S.eigen_dvfs(vol, W["K"], seed=W["seeds"]["dvf"], coarse=(2, 4, 4))
-    trace = S.breathing_trace(W["n_proj"], W["fps"], W["period_s"], W["amp_mm"], K=W["K"], irregular=True,
-                              drift_mm=W["drift_mm"], jitter=W["jitter"], amp_jitter=W["amp_jitter"],
-                              seed=W["seeds"]["trace"])
-    train = S.breathing_trace(400, W["fps"], W["period_s"], W["amp_mm"], K=W["K"], t0=0.37)
-    angles = S.gantry_angles(W["n_proj"], 360.0)
+    vol, f0, c_ref, U, trace, train, angles = precision_inputs()
     d = W["det"]
     views = [S.cone_beam(d[0], d[1], d[2], d[3], float(a)) for a in angles]
     step = 0.5 * min(W["vol"][3:])
@@ -578,13 +669,12 @@ def run_precision(args, local):
     tf0 = torch.from_numpy(f0.ravel()).to(dev)
     tU = torch.from_numpy(U.ravel()).to(dev)
     ys = torch.empty((n_used, M), dtype=torch.float32, device=dev)
-    c_true = np.zeros((n_used, 3))
+    c_true = truth("precision", trace, c_ref, U)
     for t in range(n_used):
         f = P.warp_volume(tf0, P.pca_dvf(None, tU, trace[t], vol), vol)
         p = P.drr_siddon(f, vol, views[t]) if args.projector == "siddon" else P.drr_forward(f, vol, views[t], step)
         sigma = W["noise"] * float(p.abs().max())
         ys[t] = p + torch.from_numpy(S.gaussian_noise(M, sigma, seed=1000 * W["seeds"]["noise"] + t)).to(dev)
-        c_true[t], _ = P.localize_tumor(None, tU, trace[t], vol, c_ref)
     c_lp = P.lp_fit(train, 2)
     prm = P.default_params(step)
     wsp = P.Workspace(vol, views[0], K, device=dev)
@@ -686,24 +776,16 @@ def run_batch(args, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     W = BATCH
-    g = S.rng(99)
     models = {}
-    probs = []
-    for i in range(W["n"]):
-        nx, ny, nz = W["sizes"][i % 3]
-        K = W["Ks"][i % 2]
-        nu, nv = W["dets"][i % 4]
-        vol = S.volume(nx, ny, nz, W["fov"][0] / nx, W["fov"][0] / ny, W["fov"][1] / nz)
-        key = (i % 3, K)
+    probs = batch_inputs()
+    c_true_all = truth("batch", *batch_fingerprint_parts(probs))
+    for i, pb in enumerate(probs):
+        pb["c_true"] = c_true_all[i]
+        key = pb["model"]
         if key not in models:
-            coarse = (1, 1, 1) if nx <= 128 else (2, 2, 2)
-            U = S.eigen_dvfs(vol, K, seed=200 + 10 * (i % 3) + K, coarse=coarse)
-            models[key] = torch.from_numpy(U.ravel()).to(dev)
-        f0, c_ref = S.phantom(vol, 15.0, seed=100 + i)
-        cb = S.cone_beam(nu, nv, 400.0 / nu, 400.0 / nu, float(g.uniform(0, 2 * np.pi)))
-        w_true = g.standard_normal(K)
-        probs.append(dict(vol=vol, K=K, cb=cb, f0=torch.from_numpy(f0.ravel()).to(dev), U=models[key],
-                          c_ref=c_ref, w_true=w_true, step=0.5 * min(vol["sx"], vol["sy"], vol["sz"])))
+            models[key] = torch.from_numpy(pb["U"].ravel()).to(dev)
+        pb["U"] = models[key]
+        pb["f0"] = torch.from_numpy(pb["f0"].ravel()).to(dev)
     for i, pb in enumerate(probs):
         M = pb["cb"]["nu"] * pb["cb"]["nv"]
         f = P.warp_volume(pb["f0"], P.pca_dvf(None, pb["U"], pb["w_true"], pb["vol"]), pb["vol"])
@@ -711,7 +793,6 @@ def run_batch(args, local):
              else P.drr_forward(f, pb["vol"], pb["cb"], pb["step"]))
         sigma = W["noise"] * float(p.abs().max())
         pb["y"] = p + torch.from_numpy(S.gaussian_noise(M, sigma, seed=300 + i)).to(dev)
-        pb["c_true"], _ = P.localize_tumor(None, pb["U"], pb["w_true"], pb["vol"], pb["c_ref"])
         pb["prm"] = P.default_params(pb["step"], max_iter=20)     # cold starts: 20 iterations, as the tiny case
     # one autotune per size bucket (volume, detector, K), on its first problem
     t0 = time.perf_counter()

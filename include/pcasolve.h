@@ -147,9 +147,10 @@ int cost_grad_f0(const float* f0, const float* mean, const float* U, int K, cons
                  void* stream);
 
 /* cost_grad without a caller workspace: the paper has no counterpart.  For
- * callers that cannot allocate device memory -- code recorded into a CUDA
- * graph by stream capture, real-time loops where an allocation could stall,
- * or host programs whose own allocator owns the device memory.  The scratch
+ * callers that cannot allocate device memory -- real-time loops where an
+ * allocation could stall the frame, or host programs (a treatment-machine
+ * controller, an embedding framework) whose own allocator owns all device
+ * memory and hands none to libraries.  The scratch
  * is a file-scope __device__ array of PCAS_STATIC_SCRATCH_BYTES (16 MiB) in
  * the library, which every GPU that loads the library holds until exit; no
  * call here allocates.  Volumes and detectors whose scratch
@@ -161,7 +162,8 @@ int cost_grad_f0(const float* f0, const float* mean, const float* U, int K, cons
  * capture.  All calls on a device share the array and it keeps the last
  * call's contents; each call clears what must start at zero.  Calls that
  * overlap on the GPU (other streams, other host threads) race on it.
- * Arguments, outputs and errors as cost_grad.  Synchronous. */
+ * Arguments, outputs and errors as cost_grad.  Synchronous: it waits for its
+ * work on `stream` and returns J, dJdw and ab on the host. */
 #define PCAS_STATIC_SCRATCH_BYTES (16 * 1024 * 1024)
 int cost_grad_static(const float* f0, const float* mean, const float* U, int K, const double* w,
                      const float* y, const pcas_vol* vol, const pcas_cb* cb, double step_mm,
@@ -303,15 +305,6 @@ int lp_fit(const double* trace, int T, int K, int L, double* c);
 /* Eq. (3): w0[k] = sum_l c[k][l-1] hist[l-1][k], hist[l-1] = w*(t-l) (host). */
 int lp_predict(const double* hist, const double* c, int K, int L, double* w0);
 
-/* ------------------------------------------------------------------------
- * Benchmark instrumentation (the paper has no counterpart).  The library
- * counts every kernel it launches, per kernel class.  pcas_profile(1) resets
- * the counts and, until pcas_profile(0), also brackets each launch with a
- * pair of CUDA events recorded on the launch stream (events come from a pool
- * created on the first pcas_profile(1); up to 65536 launches are timed).
- * pcas_profile_read() returns the launches and the summed event time in ms
- * of one class since the last reset; it waits for the recorded events.
- * These calls are host-side and thread-safe. */
 /* ---------------------------------------------------------------- autotuner
  * Launch shapes of the solver kernels, kept per size bucket (volume extents
  * in steps of 32, 32, 16 voxels, detector extents in steps of 64 pixels, K,
@@ -373,6 +366,15 @@ int pcas_tuning_set(const pcas_vol* vol, const pcas_cb* cb, int K, int dtype, co
 /* Forgets every stored entry. */
 int pcas_tuning_clear(void);
 
+/* ------------------------------------------------------------------------
+ * Benchmark instrumentation (the paper has no counterpart).  The library
+ * counts every kernel it launches, per kernel class.  pcas_profile(1) resets
+ * the counts and, until pcas_profile(0), also brackets each launch with a
+ * pair of CUDA events recorded on the launch stream (events come from a pool
+ * created on the first pcas_profile(1); up to 65536 launches are timed).
+ * pcas_profile_read() returns the launches and the summed event time in ms
+ * of one class since the last reset; it waits for the recorded events.
+ * These calls are host-side and thread-safe. */
 enum {
     PCAS_K_WARP_PCA = 0,     /* fused Eq. (1) + (A.5) into the solver volume   */
     PCAS_K_DRR_SOLVER = 1,   /* solver P with fused moments / Armijo test      */

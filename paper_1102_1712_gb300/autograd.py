@@ -2,7 +2,8 @@
 
 ``pca_cost(w, f0, ...)`` returns J*(w, f0) = min over (a, b) of
 ||P f(w, f0) - a y - b||^2, with (a, b) from Eq. (A.1), as a 0-d float64
-tensor.  Gradients flow to ``w`` (CPU float64, K) and to the reference CT
+tensor.  Gradients flow to ``w`` (float64, K, on the CPU or a GPU: its
+gradient is returned on w's device) and to the reference CT
 ``f0`` (CUDA float32, N).  Because (a, b) minimise J for fixed (w, f0), the
 gradients of J* are the partial derivatives at that (a, b): dJ/dw is the
 gradient below Eq. (A.2) and dJ/df0 = W^T (2 P^T r) (warp transpose of the
@@ -21,7 +22,10 @@ from . import pcasolve as P
 
 
 class _Problem:
-    """Fixed inputs of one cost: motion model, measured image and geometry."""
+    """Fixed inputs of one cost: motion model, measured image and geometry.
+    Its device workspace serves every cost built on it, one call at a time:
+    two costs of one problem evaluated concurrently (other streams or host
+    threads) would race on it, so give each concurrent user its own problem."""
 
     def __init__(self, U, y, vol, cb, step, mean=None):
         self.U, self.y, self.vol, self.cb, self.step, self.mean = U, y, vol, cb, float(step), mean
@@ -49,7 +53,8 @@ class CostFunction(torch.autograd.Function):
         wv = w.detach().cpu().double().numpy()
         _, G, _, dJdf0 = P.cost_grad_f0(f0.detach(), prob.mean, prob.U, wv, prob.y, prob.vol, prob.cb,
                                         prob.step, want_grad=True, want_grad_f0=need_f0, ws=prob.ws)
-        gw = (torch.from_numpy(np.asarray(G)).to(w.dtype) * gJ.to("cpu", w.dtype)) if need_w else None
+        gw = ((torch.from_numpy(np.asarray(G)).to(w.dtype) * gJ.detach().to("cpu", w.dtype)).to(w.device)
+              if need_w else None)
         gf0 = (dJdf0 * gJ.to(dJdf0.device, torch.float32)).view_as(f0) if need_f0 else None
         return gw, gf0, None
 

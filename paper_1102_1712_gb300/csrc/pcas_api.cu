@@ -1112,9 +1112,9 @@ int pcas_tuning_clear(void) {
 
 // ---------------------------------------------------------------------------
 // cost_grad_static: cost_grad for callers that cannot allocate device memory
-// (code running inside CUDA stream capture, real-time loops where allocation
-// is forbidden, or host programs whose allocator owns all device memory).  Its
-// scratch is the file-scope array below instead of a caller workspace.
+// (real-time loops where an allocation could stall, or host programs whose own
+// allocator owns all device memory).  Its scratch is the file-scope array
+// below instead of a caller workspace.
 }  // extern "C"
 
 namespace {

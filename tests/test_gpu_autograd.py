@@ -77,6 +77,11 @@ def test_autograd_tiny_against_oracle_and_fd(P):
     w2 = w.detach().clone().requires_grad_(True)
     (3.0 * pca_cost(w2, d["f0"], prob)).backward()
     np.testing.assert_allclose(w2.grad.numpy(), 3.0 * w.grad.numpy(), rtol=1e-12)
+    # w on the GPU: its gradient comes back on w's device
+    w3 = w.detach().cuda().requires_grad_(True)
+    pca_cost(w3, d["f0"], prob).backward()
+    assert w3.grad.is_cuda
+    np.testing.assert_allclose(w3.grad.cpu().numpy(), w.grad.numpy(), rtol=1e-12)
 
 
 @pytest.fixture(scope="module")
