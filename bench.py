@@ -68,6 +68,10 @@ def parse():
                     help="renderer of the measured images: Siddon's exact path (Sec. II.B, no inverse "
                          "crime) or the solver's own trilinear projector")
     ap.add_argument("--angle-deg", type=float, default=90.0, help="gantry angle of the fluoro workload")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="sequence workload: leave out the short batch and precision sub-objects")
+    ap.add_argument("--no-view-cache", action="store_true",
+                    help="fluoro workload: compute P^T's weights in every gradient instead of caching them")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shapes instead of tuning the size bucket first")
     ap.add_argument("--tuning", default=None,
@@ -400,6 +404,15 @@ def run_ours(args, ws_, rank, local):
     else:
         P.tuning_clear()
     solver = P.Solver(tf0, None, tU, vol, view(0.0), prm, device=dev)
+    view_cache = None
+    if args.workload == "fluoro" and not args.no_view_cache:
+        # Sec. IV: the gantry is held still, so the constant part of P^T (every
+        # voxel's footprint and ray weights) is computed once and kept
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nbytes = solver.fix_view(float(angles[0]))
+        torch.cuda.synchronize()
+        view_cache = {"bytes": nbytes, "build_s": round(time.perf_counter() - t0, 3)}
 
     def solve_range(t0, t1, hist, y_of, stats_out):
         """Host-driven sequence driver (every kernel launched and timed from the
@@ -443,6 +456,20 @@ def run_ours(args, ws_, rank, local):
     timed = [(W_ + i, st, c) for i, (w, st, c, _) in enumerate(res)]
     launches_timed = sum(n for n, _ in P.profile_read().values())
     clocks = clk.summary()
+    if view_cache is not None:
+        # the same run without the cache: bitwise the same solutions, every P^T
+        # weight recomputed in each gradient
+        solver.fix_view(None)
+        solver.seq_begin(c_lp, c_ref, w_hist=[hist[W_ - 1], hist[W_ - 2]])
+        torch.cuda.synchronize()
+        u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        u0.record(stream)
+        res_u = solver.solve_sequence([ys[t] for t in range(W_, n_used)], angles[W_:n_used])
+        u1.record(stream)
+        torch.cuda.synchronize()
+        view_cache["uncached_value"] = round(K_ / (u0.elapsed_time(u1) / 1e3), 3)
+        view_cache["same_solutions"] = all(np.array_equal(a[0], b[0]) for a, b in zip(res, res_u))
+        solver.fix_view(float(angles[0]))
 
     # ---- the same projections host-driven, every kernel bracketed by CUDA events
     P.profile(True)
@@ -548,6 +575,7 @@ def run_ours(args, ws_, rank, local):
                      "note": "kernel durations from CUDA events in the host-driven pass over the same "
                              "projections (graph launches cannot be bracketed per kernel)"},
         "host_driven": {"value": round(K_ / (ms_host / 1e3), 3), "ms_per_step": round(ms_host / K_, 4)},
+        **({"view_cache": view_cache} if view_cache is not None else {}),
         "launch_shapes": {"autotuned": tuning is not None, "given": bool(args.tuning), "tune_s": round(tune_s, 2),
                           "entry": tuning or P.tuning_get(vol, view(0.0), K)},
         "kernels": kernels,
@@ -842,6 +870,31 @@ def run_batch(args, local):
     launches = sum(n for n, _ in P.profile_read().values())
     ms_s, seq = timed(one_after_another_host, reps)
     ms_g, _ = timed(one_after_another_graph, reps)
+    # per-kernel roofline: each problem's host-driven solve with every kernel
+    # bracketed by CUDA events, bytes from that problem's own sizes
+    pk, pk_kind = peaks()
+    agg = {}
+    for i, pb in enumerate(probs):
+        P.profile(True)
+        P.solve_projection(pb["f0"], None, pb["U"], pb["y"], pb["vol"], pb["cb"], np.zeros(pb["K"]), pb["prm"],
+                           ws=wsps[i])
+        prof = P.profile_read()
+        P.profile(False)
+        v = pb["vol"]
+        kb = kernel_bytes(v["nx"] * v["ny"] * v["nz"], pb["cb"]["nu"] * pb["cb"]["nv"], pb["K"], has_mean=False)
+        for name in kb:
+            cnt, tot = prof[name]
+            a = agg.setdefault(name, [0, 0.0, 0.0])
+            a[0] += cnt
+            a[1] += tot
+            a[2] += cnt * kb[name]
+    kern = {name: {"launches": c, "total_ms": round(t, 3), "alg_bytes": int(by),
+                   "achieved_gbs": round(by / (t * 1e-3) / 1e9, 1), "frac_hbm": round(by / (t * 1e-3) / 1e9 / pk["hbm_gbs"], 4)}
+            for name, (c, t, by) in agg.items() if c}
+    dom = max(kern, key=lambda k: kern[k]["total_ms"])
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["achieved_gbs"], "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": kern[dom]["frac_hbm"], "traffic": None, "peak_source": pk_kind,
+                "note": "host-driven solves of the 64 problems, every kernel bracketed by CUDA events"}
     n = W["n"]
     errs = []
     for i, pb in enumerate(probs):
@@ -867,6 +920,7 @@ def run_batch(args, local):
             "solver": {"iters_mean": round(float(np.mean([s["iters"] for s in sts])), 3),
                        "evals_mean": round(float(np.mean([s["evals"] for s in sts])), 3)},
             "launch_shapes": {"autotuned_buckets": len(tuned), "tune_s": round(tune_s, 2)},
+            "roofline": roofline, "kernels": kern,
             "gpu_launches": launches, "clocks": clk.summary()}
 
 
@@ -945,6 +999,34 @@ def run_oracle_timing(args):
     return out
 
 
+def extra_workloads(args, local):
+    """The batch and precision workloads in short form beside the sequence
+    line: 64 uneven solves in one launch (one warm-up launch, one timed), and
+    3 + 10 projections of the precision workload per storage type.  Each
+    sub-object keeps its throughput, roofline of the dominant kernel, mm error
+    and clocks; about a minute of set-up and timing together."""
+    import copy
+    out = {}
+    a = copy.copy(args)
+    a.steps, a.warmup = 1, 1
+    b = run_batch(a, local)
+    out["batch"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "one_after_another", "speedup_vs_host_driven",
+                                      "mm_error", "solver", "gpu_launches", "clocks")}
+    out["batch"]["workload"] = b["config"]["workload"]
+    if "roofline" in b:
+        out["batch"]["roofline"] = b["roofline"]
+    a = copy.copy(args)
+    a.steps, a.warmup = 10, 3
+    p = run_precision(a, local)
+    out["precision"] = {"workload": p["config"]["workload"], "unit": "projections/s", "roofline": p["roofline"],
+                        "clocks": p["clocks"],
+                        "storage": {k: {kk: v[kk] for kk in ("value", "ms_per_step", "mm_error", "kernels") if kk in v}
+                                    | ({"centroid_vs_float32_mm_max": v["centroid_vs_float32_mm_max"]}
+                                       if "centroid_vs_float32_mm_max" in v else {})
+                                    for k, v in p["storage"].items()}}
+    return out
+
+
 def main():
     args = parse()
     ws_, rank, local = dist_env()
@@ -961,6 +1043,8 @@ def main():
         line = run_oracle_timing(args) if rank == 0 else None
     else:
         line = run_ours(args, ws_, rank, local)
+        if line is not None and ws_ == 1 and args.workload == "sequence" and not args.no_extra:
+            line.update(extra_workloads(args, local))
     if line is not None:
         print(json.dumps(line), flush=True)
     if ws_ > 1 and args.impl == "ours":

@@ -233,6 +233,26 @@ int pcas_solver_solve(pcas_solver solver, const float* y, double angle_rad, doub
                       const double* w_init, double* w_out, pcas_stats* stats, void* stream);
 int pcas_solver_destroy(pcas_solver solver);
 
+/* Fixed-angle fluoroscopy (Sec. IV: with the gantry held still the projection
+ * matrix is constant).  A solver can keep the constant part of P^T for one
+ * view -- the solver's detector at angle_rad with its creation offsets -- in
+ * a caller-provided device cache: for every voxel its footprint on the
+ * detector and the weight of each footprint ray in the gather of the
+ * gradient (the sum over the ray's samples of the voxel's trilinear weight).
+ * Solves staged at exactly that angle and those offsets (pcas_solver_solve,
+ * runs, batches) then read these weights instead of recomputing them; the
+ * sums keep their order, so results are bitwise those of the uncached solver.
+ * pcas_solver_fixed_view_bytes: device bytes of the cache for angle_rad (0 if
+ *   the solver or the view is invalid, or a detector side exceeds 32767
+ *   pixels).  Counts on the device on `stream`; synchronous.
+ * pcas_solver_fix_view: builds the cache (cache: device, 256-byte aligned,
+ *   at least pcas_solver_fixed_view_bytes; owned by the caller, valid until
+ *   the solver is destroyed or the cache is replaced); cache = NULL turns it
+ *   off.  Synchronous.  Both calls use the solver's own scratch: not while a
+ *   solve of this solver is in flight on another stream. */
+size_t pcas_solver_fixed_view_bytes(pcas_solver solver, double angle_rad, void* stream);
+int pcas_solver_fix_view(pcas_solver solver, double angle_rad, void* cache, size_t cache_bytes, void* stream);
+
 /* Runs of consecutive projections on one solver (a breathing sequence): the
  * warm start of Eq. (3) runs inside the graph, from the solutions the run
  * keeps on the device, and the tumour localisation of Sec. II.A follows each

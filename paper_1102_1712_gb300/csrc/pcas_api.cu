@@ -179,6 +179,9 @@ int make_view(const pcas_vol* vol, const pcas_cb* cb, double step, View* V) {
     V->lw1 = V->lw4 = 3;
     V->chunk1 = 0;
     V->chunk4 = 16;
+    V->pt_rect = nullptr;                   // no fixed-view cache: pcas_solver_fix_view
+    V->pt_off = nullptr;
+    V->pt_w = nullptr;
     return PCAS_OK;
 }
 
@@ -1473,6 +1476,13 @@ struct pcas_solver_s {
     View view0;           // geometry at creation (grid sizes)
     Tune tune;            // launch shapes of the size bucket at creation (captured)
     int layout;           // swap of the last staged view; -1: buffers all zero
+    // fixed-view cache of P^T (caller memory; pcas_solver_fix_view): used by
+    // the solves staged at exactly this angle and the creation offsets
+    int pt_on;
+    double pt_angle;
+    const short4* pt_rect;
+    const unsigned long long* pt_off;
+    const float* pt_w;
 };
 
 struct pcas_batch_s {
@@ -1594,6 +1604,11 @@ int solver_stage(pcas_solver s, double angle_rad, double off_u, double off_v, co
     if (w_init) PCAS_TRY(check_finite(w_init, s->K, "w_init"));
     else if (!seq) return fail(PCAS_ERR_INVALID_ARG, "w_init is NULL");
     set_layouts(V, s->tune, angle_rad);
+    if (s->pt_on && angle_rad == s->pt_angle && off_u == s->cb.off_u && off_v == s->cb.off_v) {
+        V.pt_rect = s->pt_rect;           // the fixed view: the gather reads the cached P^T
+        V.pt_off = s->pt_off;
+        V.pt_w = s->pt_w;
+    }
     int slot;
     PCAS_TRY(solver_slot(s, &slot));
     const int lay = V.swap;
@@ -1733,6 +1748,110 @@ int pcas_solver_create(pcas_solver* out, const void* f0, const void* mean, const
 }
 
 float* pcas_solver_y_buffer(pcas_solver s) { return s ? s->y : nullptr; }
+
+}  // extern "C"
+
+namespace {
+
+// Layout of a fixed-view cache of total footprint entries `total` for N voxels.
+struct PtLayout {
+    size_t off, rect, w, err, bytes;
+};
+PtLayout pt_layout(long N, unsigned long long total) {
+    PtLayout L;
+    L.off = 0;
+    L.rect = L.off + align256((size_t)(N + 1) * sizeof(unsigned long long));
+    L.w = L.rect + align256((size_t)N * sizeof(short4));
+    L.err = L.w + align256((size_t)total * sizeof(float));
+    L.bytes = L.err + 256;
+    return L;
+}
+
+// The view of a fixed-view cache (creation view at this angle), checked.
+int pt_view(pcas_solver s, double angle_rad, View* V) {
+    pcas_cb cb = s->cb;
+    cb.angle_rad = angle_rad;
+    PCAS_TRY(make_view(&s->vol, &cb, s->prm.step_mm, V));
+    if (cb.nu > 32767 || cb.nv > 32767)
+        return fail(PCAS_ERR_INVALID_ARG, "fixed-view cache: detector sides must be at most 32767 pixels");
+    return PCAS_OK;
+}
+
+// Footprint sizes of every voxel for this view, counted on the device into
+// the solver's compacted-voxel scratch (free between solves; it holds at
+// least N ints), then scanned: offsets into off (may be null) and the total
+// into *d_total (device).
+int pt_scan(pcas_solver s, const View& V, unsigned long long* off, unsigned long long* d_total, cudaStream_t st) {
+    const Grid g = make_grid(&s->vol);
+    const long N = (long)g.nx * g.ny * g.nz;
+    unsigned int* area = reinterpret_cast<unsigned int*>(s->W.adj.act_idx);
+    PCAS_LAUNCH(PCAS_K_INIT, st, launch_pt_count(V, g, area, st));
+    PCAS_LAUNCH(PCAS_K_INIT, st, launch_pt_scan(area, N, off, d_total, st));
+    return PCAS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t pcas_solver_fixed_view_bytes(pcas_solver s, double angle_rad, void* stream) {
+    if (!s) return 0;
+    View V;
+    if (pt_view(s, angle_rad, &V) != PCAS_OK) return 0;
+    cudaStream_t st = as_stream(stream);
+    // the total lands in the gather's partials (free between solves)
+    unsigned long long* d_total = reinterpret_cast<unsigned long long*>(s->W.part_adj);
+    unsigned long long total = 0;
+    if (pt_scan(s, V, nullptr, d_total, st) != PCAS_OK) return 0;
+    if (cudaMemcpyAsync(&total, d_total, sizeof(total), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return 0;
+    const long N = (long)s->vol.nx * s->vol.ny * s->vol.nz;
+    return pt_layout(N, total).bytes;
+}
+
+int pcas_solver_fix_view(pcas_solver s, double angle_rad, void* cache, size_t cache_bytes, void* stream) {
+    PCAS_TRY(check_ptr(s, "solver"));
+    cudaStream_t st = as_stream(stream);
+    PCAS_CUDA(cudaStreamSynchronize(st));         // no queued solve still reads the previous cache
+    PCAS_CUDA(cudaStreamSynchronize(s->loc_stream));
+    s->pt_on = 0;
+    if (!cache) return PCAS_OK;                   // NULL: back to computing P^T in every gather
+    if (((uintptr_t)cache & 255u) != 0) return fail(PCAS_ERR_INVALID_ARG, "fixed-view cache must be 256-byte aligned");
+    if (!isfinite(angle_rad)) return fail(PCAS_ERR_INVALID_ARG, "angle_rad must be finite");
+    View V;
+    PCAS_TRY(pt_view(s, angle_rad, &V));
+    const Grid g = make_grid(&s->vol);
+    const long N = (long)g.nx * g.ny * g.nz;
+    char* b = static_cast<char*>(cache);
+    // the N + 1 offsets go to the start of the cache, the total to their end
+    if (cache_bytes < pt_layout(N, 0).bytes)
+        return fail(PCAS_ERR_INVALID_ARG, "fixed-view cache too small: %zu bytes", cache_bytes);
+    unsigned long long* off = reinterpret_cast<unsigned long long*>(b);
+    PCAS_TRY(pt_scan(s, V, off, off + N, st));
+    unsigned long long total = 0;
+    PCAS_CUDA(cudaMemcpyAsync(&total, off + N, sizeof(total), cudaMemcpyDeviceToHost, st));
+    PCAS_CUDA(cudaStreamSynchronize(st));
+    const PtLayout L = pt_layout(N, total);
+    if (cache_bytes < L.bytes)
+        return fail(PCAS_ERR_INVALID_ARG, "fixed-view cache too small: %zu < %zu bytes (pcas_solver_fixed_view_bytes)",
+                    cache_bytes, L.bytes);
+    short4* rect = reinterpret_cast<short4*>(b + L.rect);
+    float* w = reinterpret_cast<float*>(b + L.w);
+    int* err = reinterpret_cast<int*>(b + L.err);
+    PCAS_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    PCAS_LAUNCH(PCAS_K_INIT, st, launch_pt_build(V, g, off, rect, w, err, st));
+    int herr = 0;
+    PCAS_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PCAS_CUDA(cudaStreamSynchronize(st));
+    if (herr) return fail(PCAS_ERR_CUDA, "fixed-view cache: a footprint did not match its counted size");
+    s->pt_rect = rect;
+    s->pt_off = off;
+    s->pt_w = w;
+    s->pt_angle = angle_rad;
+    s->pt_on = 1;
+    return PCAS_OK;
+}
 
 int pcas_solver_solve(pcas_solver s, const float* y, double angle_rad, double off_u, double off_v,
                       const double* w_init, double* w_out, pcas_stats* stats, void* stream) {

@@ -30,6 +30,12 @@ struct View {
                              // (see solver_pad), chosen per angle
     int lw1, lw4;            // projector warp patches (ray_pixel), chosen per angle
     int chunk1, chunk4;      // projector chunks (ray_sums_staged), chosen per angle
+    // Fixed-view cache of P^T (null: the gather computes the weights): per
+    // voxel (world index) its footprint on the detector and, from an offset in
+    // floats, the weight of every ray of that rectangle, row by row.
+    const short4* pt_rect;   // iu0, iv0, iu1, iv1 (empty when iu0 > iu1 or iv0 > iv1)
+    const unsigned long long* pt_off;
+    const float* pt_w;
 };
 
 struct Grid {
@@ -383,10 +389,12 @@ __device__ __forceinline__ void solver_frame(View& V, Grid& g, Pad& pd, int swap
     pd = make_pad(g.nx, g.ny, g.nz);
 }
 
-// Unit ray direction of pixel (iu, iv) in voxel units per mm.
+// Unit ray direction of pixel (iu, iv) in voxel units per mm.  Every
+// operation is explicit (no contraction left to the compiler), so each kernel
+// that calls it gets the same bits for a ray.
 __device__ __forceinline__ float3 ray_dir(const View& V, int iu, int iv) {
     float u = fmaf((float)iu, V.du, V.u0), v = fmaf((float)iv, V.dv, V.v0);
-    float inv = 1.0f / sqrtf(V.sdd2 + u * u + v * v);
+    float inv = 1.0f / sqrtf(fmaf(v, v, fmaf(u, u, V.sdd2)));
     float3 D;
     D.x = fmaf(u, V.Bu.x, fmaf(v, V.Bv.x, V.A.x)) * inv;
     D.y = fmaf(u, V.Bu.y, fmaf(v, V.Bv.y, V.A.y)) * inv;
@@ -639,6 +647,16 @@ cudaError_t launch_grad_f0(const float4* rayt, Grid g, const View* V, const floa
 cudaError_t launch_localize(const float* mean, const float* U, int K, const double* w, Grid g,
                             const double o[3], const double s_mm[3], const double c_ref[3],
                             int max_iter, double tol, double* out, cudaStream_t s);
+
+// Fixed-view P^T cache (View::pt_*): footprint sizes of every voxel (world
+// order) into area, their exclusive scan into off (may be null) with the total
+// into *total, and the footprints and weights themselves (err set when a
+// footprint does not fit its slot, off[n + 1] - off[n]).
+cudaError_t launch_pt_count(const View& V, Grid g, unsigned int* area, cudaStream_t s);
+cudaError_t launch_pt_scan(const unsigned int* area, long n, unsigned long long* off, unsigned long long* total,
+                           cudaStream_t s);
+cudaError_t launch_pt_build(const View& V, Grid g, const unsigned long long* off, short4* rect, float* w, int* err,
+                            cudaStream_t s);
 
 // Number of partial slots each solver kernel needs (sizes the workspace).
 enum { DRR_PART_VALS = 4 * TRIAL_BATCH + 2 };   // per-volume Sp, Syp, Spp, Srr + Sy, Syy

@@ -98,6 +98,8 @@ _SIGS = {
     "pcas_solver_solve": (C.c_int, [C.c_void_p, _P, C.c_double, C.c_double, C.c_double, _D, _D,
                                     C.POINTER(Stats), _P]),
     "pcas_solver_destroy": (C.c_int, [C.c_void_p]),
+    "pcas_solver_fixed_view_bytes": (C.c_size_t, [C.c_void_p, C.c_double, _P]),
+    "pcas_solver_fix_view": (C.c_int, [C.c_void_p, C.c_double, _P, C.c_size_t, _P]),
     "pcas_solver_seq_begin": (C.c_int, [C.c_void_p, _D, C.c_int, _D, C.c_int, C.c_double, _D, C.c_int, _P]),
     "pcas_solver_seq_enqueue": (C.c_int, [C.c_void_p, _P, C.c_double, _D, C.POINTER(C.c_longlong), _P]),
     "pcas_solver_seq_result": (C.c_int, [C.c_void_p, C.c_longlong, _P]),
@@ -459,6 +461,29 @@ class Solver:
                                        w0.ctypes.data_as(_D), w_out.ctypes.data_as(_D), C.byref(st),
                                        _stream(stream)))
         return w_out, {k: getattr(st, k) for k, _ in Stats._fields_}
+
+    # ---- fixed-angle fluoroscopy (Sec. IV): the constant part of P^T cached
+    def fixed_view_bytes(self, angle, stream=None):
+        """Device bytes of the fixed-view cache of P^T at this gantry angle."""
+        n = int(lib().pcas_solver_fixed_view_bytes(self.h, float(angle), _stream(stream)))
+        if n == 0:
+            raise ValueError("no fixed-view cache for this solver and angle: " + last_error())
+        return n
+
+    def fix_view(self, angle, stream=None):
+        """Builds the fixed-view cache for solves at exactly this angle (device
+        memory held by the solver object); angle None turns it off."""
+        import torch
+        if angle is None:
+            _check(lib().pcas_solver_fix_view(self.h, 0.0, None, 0, _stream(stream)))
+            self.pt_buf = None
+            return 0
+        n = self.fixed_view_bytes(angle, stream)
+        buf = torch.empty(n + 256, dtype=torch.uint8, device=self.buf.device)
+        ptr = (buf.data_ptr() + 255) & ~255
+        _check(lib().pcas_solver_fix_view(self.h, float(angle), ptr, n, _stream(stream)))
+        self.pt_buf = buf
+        return n
 
     # ---- runs of consecutive projections (warm start and localisation on the device)
     def seq_begin(self, lp_coef, c_ref, loc_max_iter=50, loc_tol_mm=1e-6, w_hist=None, stream=None):
