@@ -622,7 +622,9 @@ def cpu_baseline(vol, f0, c_ref, U, trace, train, angles, ys, t):
     dt = time.perf_counter() - t0
     line = {"value": round(1.0 / dt, 5), "unit": "projections/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"1 projection (#{t}) of the same workload, full solve ({st['iters']} iterations, "
-                      f"{st['evals']} evaluations) + localisation, {dt:.1f} s"}
+                      f"{st['evals']} evaluations) + localisation, {dt:.1f} s; OpenMP over the rays of the "
+                      "forward projector and the voxels of the DVF and warp, the P^T scatter and the "
+                      "gradient reduction serial (their sums in written order)"}
     return line, {"w0": w0, "w": np.asarray(w), "c": np.asarray(c), "J": st["J"], "iters": st["iters"],
                   "evals": st["evals"]}
 
@@ -670,7 +672,10 @@ def run_reference(args, ws_, rank):
             "data": "synthetic, same workload as our arm", "config": {"workload": workload_name(args)},
             "cpu_baseline": {"value": round(value, 5), "unit": "projections/s", "cores": os.cpu_count(),
                              "kind": "oracle",
-                             "sample": f"{done} projection{'s' if done != 1 else ''} of the workload, full solves, at most about 150 s of solving"},
+                             "sample": f"{done} projection{'s' if done != 1 else ''} of the workload, full solves, "
+                                       "at most about 150 s of solving; OpenMP over the rays of the forward projector "
+                                       "and the voxels of the DVF and warp, the P^T scatter and the gradient "
+                                       "reduction serial"},
             "e2e": {"value": round(value, 5), "unit": "projections/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
