@@ -8,6 +8,7 @@ namespace pcas {
 namespace {
 
 constexpr int kWarpThreads = 256;
+constexpr int kBatchVPT = 4;     // voxels per thread of the batch warp
 
 // Eq. (1) on four consecutive voxels: x_c = mean_c + sum_k w_k U_kc.
 template <typename T>
@@ -228,13 +229,13 @@ k_warp_pca(const float* __restrict__ f0h, const T* __restrict__ mean,
 // each w + mu_j d): the motion model is read once per voxel and reused for the
 // five coefficient vectors; each DVF is formed in the same operation order as
 // the single-volume warp, so a candidate's volume is bit-identical to a lone
-// evaluation.  Output: one float4 (f_0..f_3) per voxel in the candidate
+// evaluation.  Each thread takes VPT voxels of its row, blockDim.x apart.  Output: one float4 (f_0..f_3) per voxel in the candidate
 // buffer and f_4 in the one-volume buffer, zero-halo layout; the occupancy
 // bricks mark the union of the five.  All five are rendered even when fewer
 // are on the schedule (a narrow batch projects only the first two): the
 // kernel is issue-bound, and a run-time candidate count in it costs more
 // than the gathers it would save.
-template <typename T, int KT>
+template <typename T, int KT, int VPT>
 __global__ void __launch_bounds__(kWarpThreads, KT <= 3 ? 6 : (KT <= 5 ? 5 : (KT <= 7 ? 4 : 3)))
 k_warp_batch(const float* __restrict__ f0h, const T* __restrict__ mean,
              const T* __restrict__ U, const SolveState* st, Grid g, const View* __restrict__ Vp,
@@ -255,62 +256,69 @@ k_warp_batch(const float* __restrict__ f0h, const T* __restrict__ mean,
 #pragma unroll
         for (int kk = 0; kk < KT; kk++) wk[b][kk] = s_w[b][kk];
     int bx[6] = {BOX_EMPTY, BOX_EMPTY, BOX_EMPTY, BOX_EMPTY, BOX_EMPTY, BOX_EMPTY};
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    const int j = blockIdx.y, k = blockIdx.z;
     const long N = (long)g.nx * g.ny * g.nz;
-    if (i < g.nx) {
-        const int n = (k * g.ny + j) * g.nx + i;
-        float x[TRIAL_BATCH][3];
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            const float m = mean ? ldcs_f(mean + c * N + n) : 0.0f;
-#pragma unroll
-            for (int b = 0; b < TRIAL_BATCH; b++) x[b][c] = m;
-        }
-        const T* u0 = U + n;
-        float u[KT][3];
-#pragma unroll
-        for (int kk = 0; kk < KT; kk++)
-#pragma unroll
-            for (int c = 0; c < 3; c++) u[kk][c] = ldcs_f(u0 + (kk * 3 + c) * N);
-#pragma unroll
-        for (int kk = 0; kk < KT; kk++)      // Eq. (1) in the order of the single-volume warp
-#pragma unroll
-            for (int c = 0; c < 3; c++)
-#pragma unroll
-                for (int b = 0; b < TRIAL_BATCH; b++) x[b][c] = fmaf(wk[b][kk], u[kk][c], x[b][c]);
-        float q[TRIAL_BATCH][3];
-#pragma unroll
-        for (int b = 0; b < TRIAL_BATCH; b++) {
-            q[b][0] = fmaf(x[b][0], g.inv_sx, (float)i);
-            q[b][1] = fmaf(x[b][1], g.inv_sy, (float)j);
-            q[b][2] = fmaf(x[b][2], g.inv_sz, (float)k);
-        }
-        // one test for the five: when every brick their cells can lie in is
-        // empty, all eight taps of each are zero and so are the candidates
-        bool live = true;
-        if (occ.f0m) {
-            float lo[3], hi[3];
+    // VPT voxels per thread, blockDim.x apart (each pass of the loop stores
+    // coalesced rows): the per-thread set-up and the block's box reduction are
+    // shared by them
+#pragma unroll 1
+    for (int r = 0; r < VPT; r++) {
+        const int i = (blockIdx.x * VPT + r) * blockDim.x + threadIdx.x;
+        if (i < g.nx) {
+            const int n = (k * g.ny + j) * g.nx + i;
+            float x[TRIAL_BATCH][3];
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                lo[c] = hi[c] = q[0][c];
+                const float m = mean ? ldcs_f(mean + c * N + n) : 0.0f;
 #pragma unroll
-                for (int b = 1; b < TRIAL_BATCH; b++) {
-                    lo[c] = fminf(lo[c], q[b][c]);
-                    hi[c] = fmaxf(hi[c], q[b][c]);
-                }
+                for (int b = 0; b < TRIAL_BATCH; b++) x[b][c] = m;
             }
-            live = f0_box_live(occ.f0m, g, lo[0], lo[1], lo[2], hi[0], hi[1], hi[2]);
-        }
-        float o[TRIAL_BATCH];
+            const T* u0 = U + n;
+            float u[KT][3];
 #pragma unroll
-        for (int b = 0; b < TRIAL_BATCH; b++) o[b] = live ? tri_halo(f0h, g, q[b][0], q[b][1], q[b][2]) : 0.0f;
-        const int a0 = swp ? j : i, a1 = swp ? i : j;
-        const long d = pad_index(pd, a0, a1, k);
-        fpad4[d] = make_float4(o[0], o[1], o[2], o[3]);
-        fpad[d] = o[4];
-        if (o[0] != 0.0f || o[1] != 0.0f || o[2] != 0.0f || o[3] != 0.0f || o[4] != 0.0f) {
-            box_add(bx, a0, a1, k);
-            if (oc.m) occ_mark(oc.m, oc.gen, oc.nbx, oc.nby, a0, a0, a1, a1, k);
+            for (int kk = 0; kk < KT; kk++)
+#pragma unroll
+                for (int c = 0; c < 3; c++) u[kk][c] = ldcs_f(u0 + (kk * 3 + c) * N);
+#pragma unroll
+            for (int kk = 0; kk < KT; kk++)      // Eq. (1) in the order of the single-volume warp
+#pragma unroll
+                for (int c = 0; c < 3; c++)
+#pragma unroll
+                    for (int b = 0; b < TRIAL_BATCH; b++) x[b][c] = fmaf(wk[b][kk], u[kk][c], x[b][c]);
+            float q[TRIAL_BATCH][3];
+#pragma unroll
+            for (int b = 0; b < TRIAL_BATCH; b++) {
+                q[b][0] = fmaf(x[b][0], g.inv_sx, (float)i);
+                q[b][1] = fmaf(x[b][1], g.inv_sy, (float)j);
+                q[b][2] = fmaf(x[b][2], g.inv_sz, (float)k);
+            }
+            // one test for the five: when every brick their cells can lie in is
+            // empty, all eight taps of each are zero and so are the candidates
+            bool live = true;
+            if (occ.f0m) {
+                float lo[3], hi[3];
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    lo[c] = hi[c] = q[0][c];
+#pragma unroll
+                    for (int b = 1; b < TRIAL_BATCH; b++) {
+                        lo[c] = fminf(lo[c], q[b][c]);
+                        hi[c] = fmaxf(hi[c], q[b][c]);
+                    }
+                }
+                live = f0_box_live(occ.f0m, g, lo[0], lo[1], lo[2], hi[0], hi[1], hi[2]);
+            }
+            float o[TRIAL_BATCH];
+#pragma unroll
+            for (int b = 0; b < TRIAL_BATCH; b++) o[b] = live ? tri_halo(f0h, g, q[b][0], q[b][1], q[b][2]) : 0.0f;
+            const int a0 = swp ? j : i, a1 = swp ? i : j;
+            const long d = pad_index(pd, a0, a1, k);
+            fpad4[d] = make_float4(o[0], o[1], o[2], o[3]);
+            fpad[d] = o[4];
+            if (o[0] != 0.0f || o[1] != 0.0f || o[2] != 0.0f || o[3] != 0.0f || o[4] != 0.0f) {
+                box_add(bx, a0, a1, k);
+                if (oc.m) occ_mark(oc.m, oc.gen, oc.nbx, oc.nby, a0, a0, a1, a1, k);
+            }
         }
     }
     box_reduce(bx, box_out);      // every thread of the block, one call site
@@ -367,7 +375,7 @@ cudaError_t warp_batch_t(const float* f0, const T* mean, const T* U, int K, cons
                          cudaStream_t s) {
     switch (K) {
 #define PCAS_WB_CASE(KK) \
-        case KK: k_warp_batch<T, KK><<<L.grid, L.threads, 0, s>>>(f0, mean, U, st, g, Vd, fpad4, fpad, box, oc); break;
+        case KK: k_warp_batch<T, KK, kBatchVPT><<<L.grid, L.threads, 0, s>>>(f0, mean, U, st, g, Vd, fpad4, fpad, box, oc); break;
         PCAS_WB_CASE(1) PCAS_WB_CASE(2) PCAS_WB_CASE(3) PCAS_WB_CASE(4)
         PCAS_WB_CASE(5) PCAS_WB_CASE(6) PCAS_WB_CASE(7) PCAS_WB_CASE(8)
 #undef PCAS_WB_CASE
@@ -414,7 +422,7 @@ cudaError_t launch_warp_pca(const float* f0, const void* mean, const void* U, in
 cudaError_t launch_warp_batch(const float* f0, const void* mean, const void* U, int dt, int K,
                               const SolveState* st, Grid g, const View* Vd, float4* fpad4, float* fpad,
                               Occ oc, cudaStream_t s) {
-    const RowLaunch L = row_launch(g, 1);
+    const RowLaunch L = row_launch(g, kBatchVPT);
     int* box = const_cast<int*>(st->box[1]);
     PCAS_DT_DISPATCH(dt, (warp_batch_t<T>(f0, static_cast<const T*>(mean),
                                           static_cast<const T*>(U), K, st, g, Vd, fpad4, fpad, box, oc, L, s)))
