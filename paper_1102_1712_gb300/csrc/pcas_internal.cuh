@@ -280,6 +280,22 @@ __device__ __forceinline__ void taps_halo(const float* __restrict__ f, const Gri
     v[6] = __ldg(b + sz + sy); v[7] = __ldg(b + sz + sy + 1);
 }
 
+// tri_halo for a position already inside the clamp range [-2, n + 1] of every
+// axis (the clamps would not change it): the same taps and arithmetic.
+__device__ __forceinline__ float tri_halo_in(const float* __restrict__ f, const Grid& g, float qx, float qy,
+                                             float qz) {
+    const float fx = floorf(qx), fy = floorf(qy), fz = floorf(qz);
+    const float zx = qx - fx, zy = qy - fy, zz = qz - fz;
+    const int sy = g.nx + 2 * F0_HALO, sz = sy * (g.ny + 2 * F0_HALO);
+    const float* b = f + (((int)fz + F0_HALO) * sz + ((int)fy + F0_HALO) * sy + ((int)fx + F0_HALO));
+    const float v0 = __ldg(b), v1 = __ldg(b + 1), v2 = __ldg(b + sy), v3 = __ldg(b + sy + 1);
+    const float v4 = __ldg(b + sz), v5 = __ldg(b + sz + 1), v6 = __ldg(b + sz + sy), v7 = __ldg(b + sz + sy + 1);
+    const float c00 = fmaf(zx, v1 - v0, v0), c10 = fmaf(zx, v3 - v2, v2);
+    const float c01 = fmaf(zx, v5 - v4, v4), c11 = fmaf(zx, v7 - v6, v6);
+    const float c0 = fmaf(zy, c10 - c00, c00), c1 = fmaf(zy, c11 - c01, c01);
+    return fmaf(zz, c1 - c0, c0);
+}
+
 // Brick of the reference CT holding the cell that taps_halo takes at q
 // (world axes, the same clamps and floors), as an index into its mask.
 __device__ __forceinline__ int f0_brick(const Grid& g, float qx, float qy, float qz) {

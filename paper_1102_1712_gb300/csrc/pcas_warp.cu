@@ -292,25 +292,33 @@ k_warp_batch(const float* __restrict__ f0h, const T* __restrict__ mean,
                 q[b][1] = fmaf(x[b][1], g.inv_sy, (float)j);
                 q[b][2] = fmaf(x[b][2], g.inv_sz, (float)k);
             }
-            // one test for the five: when every brick their cells can lie in is
-            // empty, all eight taps of each are zero and so are the candidates
-            bool live = true;
-            if (occ.f0m) {
-                float lo[3], hi[3];
+            // the box of the five positions: one brick test for all of them
+            // (when every brick their cells can lie in is empty, all eight taps
+            // of each are zero and so are the candidates), and inside the
+            // grid's clamp range [-2, n + 1] the taps are read without clamps
+            float lo[3], hi[3];
 #pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    lo[c] = hi[c] = q[0][c];
+            for (int c = 0; c < 3; c++) {
+                lo[c] = hi[c] = q[0][c];
 #pragma unroll
-                    for (int b = 1; b < TRIAL_BATCH; b++) {
-                        lo[c] = fminf(lo[c], q[b][c]);
-                        hi[c] = fmaxf(hi[c], q[b][c]);
-                    }
+                for (int b = 1; b < TRIAL_BATCH; b++) {
+                    lo[c] = fminf(lo[c], q[b][c]);
+                    hi[c] = fmaxf(hi[c], q[b][c]);
                 }
-                live = f0_box_live(occ.f0m, g, lo[0], lo[1], lo[2], hi[0], hi[1], hi[2]);
             }
+            const bool live = !occ.f0m || f0_box_live(occ.f0m, g, lo[0], lo[1], lo[2], hi[0], hi[1], hi[2]);
+            const bool inside = lo[0] >= -2.0f && lo[1] >= -2.0f && lo[2] >= -2.0f && hi[0] <= (float)g.nx + 1.0f &&
+                                hi[1] <= (float)g.ny + 1.0f && hi[2] <= (float)g.nz + 1.0f;
             float o[TRIAL_BATCH];
 #pragma unroll
-            for (int b = 0; b < TRIAL_BATCH; b++) o[b] = live ? tri_halo(f0h, g, q[b][0], q[b][1], q[b][2]) : 0.0f;
+            for (int b = 0; b < TRIAL_BATCH; b++) o[b] = 0.0f;
+            if (live && inside) {
+#pragma unroll
+                for (int b = 0; b < TRIAL_BATCH; b++) o[b] = tri_halo_in(f0h, g, q[b][0], q[b][1], q[b][2]);
+            } else if (live) {
+#pragma unroll
+                for (int b = 0; b < TRIAL_BATCH; b++) o[b] = tri_halo(f0h, g, q[b][0], q[b][1], q[b][2]);
+            }
             const int a0 = swp ? j : i, a1 = swp ? i : j;
             const long d = pad_index(pd, a0, a1, k);
             fpad4[d] = make_float4(o[0], o[1], o[2], o[3]);
