@@ -23,8 +23,9 @@
  *   outputs are ready.
  * Volumes.  float32, layout [nz][ny][nx] (x fastest), voxel (i,j,k) centred
  *   at (ox + i sx, oy + j sy, oz + k sz) mm.  Values outside the grid are 0.
- *   Size limits (PCAS_ERR_INVALID_ARG beyond them): ny, nz <= 65535 and
- *   (m + 10)(m + 4)(nz + 4) < 2^31 with m = max(nx, ny).
+ *   Size limits (PCAS_ERR_INVALID_ARG beyond them): ny, nz <= 65535,
+ *   (m + 10)(m + 4)(nz + 4) < 2^31 with m = max(nx, ny), and
+ *   (nx + 6)(ny + 6)(nz + 6) < 2^31.
  * Motion model.  mean: [3][N] float32 mm (may be NULL = zero mean field);
  *   U: [K][3][N] float32 mm, component 0 = x (lateral), 1 = y (AP),
  *   2 = z (SI), N = nx ny nz; 1 <= K <= PCAS_KMAX.

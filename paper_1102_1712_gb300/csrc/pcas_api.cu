@@ -110,10 +110,13 @@ int check_vol(const pcas_vol* v) {
     if (!v) return fail(PCAS_ERR_INVALID_ARG, "vol is NULL");
     if (v->nx < 1 || v->ny < 1 || v->nz < 1)
         return fail(PCAS_ERR_INVALID_ARG, "volume dims must be positive (%d,%d,%d)", v->nx, v->ny, v->nz);
-    // 32-bit voxel offsets: either zero-halo layout (at most (m + 10) (m + 4) (nz + 4)
-    // elements, m = max(nx, ny)) stays below 2^31; ny, nz index grid rows
+    // 32-bit voxel offsets: either zero-halo layout of the warped volume (at
+    // most (m + 10) (m + 4) (nz + 4) elements, m = max(nx, ny)) and the
+    // reference CT's halo copy ((nx + 6) (ny + 6) (nz + 6) elements) stay below
+    // 2^31; ny, nz index grid rows
     const double m = v->nx > v->ny ? v->nx : v->ny;
-    if ((m + 10.0) * (m + 4.0) * (v->nz + 4.0) > 2147483647.0 || v->ny > 65535 || v->nz > 65535)
+    if ((m + 10.0) * (m + 4.0) * (v->nz + 4.0) > 2147483647.0 ||
+        (v->nx + 6.0) * (v->ny + 6.0) * (v->nz + 6.0) > 2147483647.0 || v->ny > 65535 || v->nz > 65535)
         return fail(PCAS_ERR_INVALID_ARG, "volume too large (%d,%d,%d): at most 2^31 voxels with halo, "
                     "ny and nz at most 65535", v->nx, v->ny, v->nz);
     if (!(v->sx > 0) || !(v->sy > 0) || !(v->sz > 0))

@@ -80,6 +80,7 @@ def test_volume_size_limits(lib):
     assert P.workspace_bytes(S.volume(8, 65536, 4, 1, 1, 1), cb, 1) == 0
     assert P.workspace_bytes(S.volume(8, 4, 65536, 1, 1, 1), cb, 1) == 0
     assert P.workspace_bytes(S.volume(1300, 1300, 1260, 1, 1, 1), cb, 1) == 0   # (1310)(1304)(1264) > 2^31
+    assert P.workspace_bytes(S.volume(20000, 20000, 1, 1, 1, 1), cb, 1) == 0    # halo copy: 20006^2 7 > 2^31
     assert P.workspace_bytes(S.volume(1024, 1024, 1024, 1, 1, 1), cb, 1) > 0
 
 

@@ -1,8 +1,8 @@
 """cost_grad_static: the cost/gradient evaluation for callers that cannot
-allocate device memory (inside CUDA stream capture, in allocation-free
-real-time loops, or under a host program that owns all device memory).  It
-must give what cost_grad gives with a caller workspace, call after call,
-although its fixed device scratch keeps the previous call's contents.
+allocate device memory (allocation-free real-time loops, or a host program
+that owns all device memory).  It must give what cost_grad gives with a
+caller workspace, call after call, although its fixed device scratch keeps
+the previous call's contents.
 
 Collected last on purpose (file name), so a run that stops at the first
 failure has already run every other test."""
