@@ -156,7 +156,7 @@ int cost_grad_f0(const float* f0, const float* mean, const float* U, int K, cons
  * the library, which every GPU that loads the library holds until exit; no
  * call here allocates.  Volumes and detectors whose scratch
  * (pcas_workspace_bytes) exceeds that size are rejected with
- * PCAS_ERR_INVALID_ARG (e.g. 80x80x40 voxels with a 192x144 detector and
+ * PCAS_ERR_INVALID_ARG (e.g. 72x72x40 voxels with a 192x144 detector and
  * K = 3 fit; 256x256x100 does not).  The first call on each device looks
  * up the array's device address (cudaGetSymbolAddress, which also loads the
  * library's device code there): make that first call before any stream

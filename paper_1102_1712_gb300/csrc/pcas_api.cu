@@ -197,7 +197,7 @@ int check_model(const void* mean, const void* U, int K) {
 
 // ------------------------------------------------------------- workspace
 struct Layout {
-    size_t state, view, f0h, f0m, fpad, fpad4, occ, pbuf, rayt, part_drr, part_res, part_adj, act_idx, act_h,
+    size_t state, view, f0h, f0m, fpad, fpair, fpad4, occ, pbuf, rayt, part_drr, part_res, part_adj, act_idx, act_h,
         tile_count, tile_off, total;
 };
 
@@ -214,6 +214,7 @@ Layout layout(const pcas_vol* vol, const pcas_cb* cb, int K) {
     L.f0h = off; off += align256((size_t)f0h_count(vol->nx, vol->ny, vol->nz) * sizeof(float));  // f0, halo 3
     L.f0m = off; off += align256((size_t)occ_count(vol->nx, vol->ny, vol->nz));     // its bricks (zeroed with it)
     L.fpad = off; off += align256(npad * sizeof(float));                 // f(w), zero halo
+    L.fpair = off; off += align256(npad * sizeof(float2));               // f(w) as x pairs (the L1 march)
     L.fpad4 = off; off += align256(npad * sizeof(float4));               // candidates 0-3 (4 in fpad)
     L.occ = off; off += align256((size_t)occ_count(vol->nx, vol->ny, vol->nz) * sizeof(unsigned int));
     L.pbuf = off; off += align256((size_t)NBUF * M * sizeof(float));     // projection ring
@@ -238,9 +239,10 @@ struct Ws {
     size_t f0h_bytes;         // f0h and f0m
     unsigned int* occ;        // occupancy bricks of the solver volumes
     float *fpad, *pbuf;
+    float2* fpair;
     float4 *fpad4, *rayt;
     double *part_drr, *part_res, *part_adj;
-    size_t fpad_bytes, fpad4_bytes;
+    size_t fpad_bytes, fpad4_bytes;      // fpad_bytes: fpad and fpair
     AdjScratch adj;
 };
 
@@ -257,6 +259,7 @@ int bind_ws(void* ws, size_t ws_bytes, const pcas_vol* vol, const pcas_cb* cb, i
     W->f0m = reinterpret_cast<unsigned char*>(b + L.f0m);
     W->f0h_bytes = L.fpad - L.f0h;
     W->fpad = reinterpret_cast<float*>(b + L.fpad);
+    W->fpair = reinterpret_cast<float2*>(b + L.fpair);
     W->fpad4 = reinterpret_cast<float4*>(b + L.fpad4);
     W->occ = reinterpret_cast<unsigned int*>(b + L.occ);
     W->pbuf = reinterpret_cast<float*>(b + L.pbuf);
@@ -277,6 +280,10 @@ int bind_ws(void* ws, size_t ws_bytes, const pcas_vol* vol, const pcas_cb* cb, i
 inline Occ occ_of(const Ws& W, const Tune& T) {
     return Occ{T.skip ? W.occ : nullptr, &W.st->occ_gen, T.skip ? W.f0m : nullptr};
 }
+
+// Where the one-volume warp writes f(w): the x-pair copy when the one-volume
+// projector marches through L1 (chunk1 = 0), else the scalar volume it stages.
+inline float2* pair_of(const Ws& W, const Tune& T) { return T.chunk1 == 0 ? W.fpair : nullptr; }
 
 // ------------------------------------------------------------ launch shapes
 // Default shapes: 8 x 4 warp patches, 16-sample chunks for the batch
@@ -519,10 +526,10 @@ int eval_gradient_pipeline(const void* f0, const void* mean, const void* U, int 
     ws.dev = W.st->w;
     ws.phase = &W.st->phase;
     PCAS_TRY(stage_f0h(f0, dt, g, W, T, s));
-    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(W.f0h, mean, U, dt, K, ws, g, W.view, W.fpad, W.st->box[0],
+    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(W.f0h, mean, U, dt, K, ws, g, W.view, W.fpad, pair_of(W, T), W.st->box[0],
                                                     occ_of(W, T), s));
     PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
-                launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, T, 0ull, 0,
+                launch_drr_solver(W.fpad, W.fpair, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, T, 0ull, 0,
                                   occ_of(W, T), s));
     PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, W.view, 1, W.rayt, W.st, W.part_res, s));
     PCAS_LAUNCH(PCAS_K_ADJ_GRAD, s,
@@ -549,10 +556,10 @@ int solve_host(const void* f0, const void* mean, const void* U, int dtype, int K
     wcur.dev = W.st->w;
     wcur.phase = &W.st->phase;
     PCAS_TRY(stage_f0h(f0, dtype, g, W, T, s));
-    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(W.f0h, mean, U, dtype, K, wcur, g, W.view, W.fpad,
+    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(W.f0h, mean, U, dtype, K, wcur, g, W.view, W.fpad, pair_of(W, T),
                                                     W.st->box[0], occ_of(W, T), s));
     PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
-                launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, T, 0ull, 0,
+                launch_drr_solver(W.fpad, W.fpair, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, T, 0ull, 0,
                                   occ_of(W, T), s));
     int iters = 0, phase = PH_RUNNING;
     for (int it = 0; it < prm->max_iter; it++) {
@@ -570,7 +577,7 @@ int solve_host(const void* f0, const void* mean, const void* U, int dtype, int K
             PCAS_LAUNCH(PCAS_K_WARP_BATCH, s, launch_warp_batch(W.f0h, mean, U, dtype, K, W.st, g, W.view,
                                                                 W.fpad4, W.fpad, occ_of(W, T), s));
             PCAS_LAUNCH(PCAS_K_DRR_BATCH, s,
-                        launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, TRIAL_BATCH, W.st, W.part_drr,
+                        launch_drr_solver(W.fpad, W.fpair, W.fpad4, g, V, W.view, y, W.pbuf, TRIAL_BATCH, W.st, W.part_drr,
                                           T, 0ull, 0, occ_of(W, T), s));
             PCAS_CUDA(cudaMemcpyAsync(&phase, &W.st->phase, sizeof(int), cudaMemcpyDeviceToHost, s));
             PCAS_CUDA(cudaStreamSynchronize(s));
@@ -806,10 +813,10 @@ int cost_grad_f0(const float* f0, const float* mean, const float* U, int K, cons
     wsrc.dev = W.st->w;
     wsrc.phase = &W.st->phase;
     PCAS_TRY(stage_f0h(f0, DT_F32, g, W, T, s));
-    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(W.f0h, mean, U, DT_F32, K, wsrc, g, W.view, W.fpad,
+    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(W.f0h, mean, U, DT_F32, K, wsrc, g, W.view, W.fpad, pair_of(W, T),
                                                     W.st->box[0], occ_of(W, T), s));
     PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
-                launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, T, 0ull, 0,
+                launch_drr_solver(W.fpad, W.fpair, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, T, 0ull, 0,
                                   occ_of(W, T), s));
     PCAS_LAUNCH(PCAS_K_RESID, s, launch_resid(W.pbuf, y, V, W.view, 1, W.rayt, W.st, W.part_res, s));
     if (dJdw)
@@ -1543,8 +1550,9 @@ int capture_solve(pcas_solver s, cudaGraph_t graph, cudaStream_t cs, const float
     WSrc wcur{};
     wcur.dev = W.st->w;
     wcur.phase = &W.st->phase;
-    PCAS_G(launch_warp_pca(W.f0h, s->mean, s->U, s->dtype, s->K, wcur, g, W.view, W.fpad, W.st->box[0], oc, cs));
-    PCAS_G(launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, s->y, W.pbuf, 0, W.st, W.part_drr, s->tune, 0ull, 0,
+    PCAS_G(launch_warp_pca(W.f0h, s->mean, s->U, s->dtype, s->K, wcur, g, W.view, W.fpad, pair_of(W, s->tune),
+                           W.st->box[0], oc, cs));
+    PCAS_G(launch_drr_solver(W.fpad, W.fpair, W.fpad4, g, V, W.view, s->y, W.pbuf, 0, W.st, W.part_drr, s->tune, 0ull, 0,
                              oc, cs));
     k_ctrl_start<<<1, 1, 0, cs>>>(W.st, s->h_outer);
     PCAS_G(cudaGetLastError());
@@ -1573,7 +1581,7 @@ int capture_solve(pcas_solver s, cudaGraph_t graph, cudaStream_t cs, const float
     // decides the batch and whether another follows
     PCAS_G(cudaStreamBeginCaptureToGraph(cs, inner_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     PCAS_G(launch_warp_batch(W.f0h, s->mean, s->U, s->dtype, s->K, W.st, g, W.view, W.fpad4, W.fpad, oc, cs));
-    PCAS_G(launch_drr_solver(W.fpad, W.fpad4, g, V, W.view, s->y, W.pbuf, TRIAL_BATCH, W.st, W.part_drr,
+    PCAS_G(launch_drr_solver(W.fpad, W.fpair, W.fpad4, g, V, W.view, s->y, W.pbuf, TRIAL_BATCH, W.st, W.part_drr,
                              s->tune, s->h_inner, 1, oc, cs));
     PCAS_G(cudaStreamEndCapture(cs, &done));
     return PCAS_OK;

@@ -351,25 +351,6 @@ __device__ __forceinline__ float tri_halo_m(const float* __restrict__ f, const u
     return tri_halo(f, g, qx, qy, qz);
 }
 
-// Same interpolant on the zero-halo layout: no bounds tests and no clamps.
-// Valid for q within half a voxel of [-1, n] (the caller guarantees it): the
-// floor is then in [-2, n] and every tap is a voxel or a halo zero.
-__device__ __forceinline__ float tri_padded(const float* __restrict__ f, const Pad& pd, float qx,
-                                            float qy, float qz) {
-    const float fx = floorf(qx), fy = floorf(qy), fz = floorf(qz);
-    const float zx = qx - fx, zy = qy - fy, zz = qz - fz;
-    const int sy = pd.px, sz = pd.px * pd.pny;
-    const float* b = f + (((int)fz + 2) * sz + ((int)fy + 2) * sy + ((int)fx + 4));
-    const float v000 = __ldg(b), v100 = __ldg(b + 1);
-    const float v010 = __ldg(b + sy), v110 = __ldg(b + sy + 1);
-    const float v001 = __ldg(b + sz), v101 = __ldg(b + sz + 1);
-    const float v011 = __ldg(b + sz + sy), v111 = __ldg(b + sz + sy + 1);
-    const float c00 = fmaf(zx, v100 - v000, v000), c10 = fmaf(zx, v110 - v010, v010);
-    const float c01 = fmaf(zx, v101 - v001, v001), c11 = fmaf(zx, v111 - v011, v011);
-    const float c0 = fmaf(zy, c10 - c00, c00), c1 = fmaf(zy, c11 - c01, c01);
-    return fmaf(zz, c1 - c0, c0);
-}
-
 __device__ __forceinline__ float lerp1(float z, float a, float b) { return fmaf(z, b - a, a); }
 __device__ __forceinline__ float4 lerp4(float z, const float4& a, const float4& b) {
     return make_float4(lerp1(z, a.x, b.x), lerp1(z, a.y, b.y), lerp1(z, a.z, b.z), lerp1(z, a.w, b.w));
@@ -388,6 +369,24 @@ __device__ __forceinline__ float4 tri_padded4(const float4* __restrict__ f, cons
     const float4 c01 = lerp4(zx, __ldg(b + sz), __ldg(b + sz + 1));
     const float4 c11 = lerp4(zx, __ldg(b + sz + sy), __ldg(b + sz + sy + 1));
     return lerp4(zz, lerp4(zy, c00, c10), lerp4(zy, c01, c11));
+}
+
+// Same interpolant on the zero-halo layout (Pad), read from its x-pair copy:
+// element e holds (f[e], f[e + 1]) of the layout (zero where either lies in
+// the halo), so the eight taps are four 8-byte loads.  No bounds tests and no
+// clamps: valid for q within half a voxel of [-1, n] (the caller guarantees
+// it), where the floor is in [-2, n] and every tap is a voxel or a halo zero.
+__device__ __forceinline__ float tri_padded_pairs(const float2* __restrict__ f, const Pad& pd, float qx,
+                                                  float qy, float qz) {
+    const float fx = floorf(qx), fy = floorf(qy), fz = floorf(qz);
+    const float zx = qx - fx, zy = qy - fy, zz = qz - fz;
+    const int sy = pd.px, sz = pd.px * pd.pny;
+    const float2* b = f + (((int)fz + 2) * sz + ((int)fy + 2) * sy + ((int)fx + 4));
+    const float2 p00 = __ldg(b), p10 = __ldg(b + sy), p01 = __ldg(b + sz), p11 = __ldg(b + sz + sy);
+    const float c00 = fmaf(zx, p00.y - p00.x, p00.x), c10 = fmaf(zx, p10.y - p10.x, p10.x);
+    const float c01 = fmaf(zx, p01.y - p01.x, p01.x), c11 = fmaf(zx, p11.y - p11.x, p11.x);
+    const float c0 = fmaf(zy, c10 - c00, c00), c1 = fmaf(zy, c11 - c01, c01);
+    return fmaf(zz, c1 - c0, c0);
 }
 
 // ----------------------------------------------------------------- rays
@@ -599,14 +598,15 @@ cudaError_t launch_warp_dvf(const void* f0, int dt, const float* dvf, Grid g, fl
 cudaError_t launch_fill_f0h(const void* f0, int dt, Grid g, float* f0h, unsigned char* f0m, const int* skip,
                             cudaStream_t s);
 // Solver warps: launch_warp_pca writes f(w_src) to the scalar zero-halo
-// buffer; launch_warp_batch writes the batch: candidates st->wt[0..3]
-// interleaved (float4) and wt[4] to fpad.
+// buffer fpad, or, when fpair is not null, to fpair as x pairs (see
+// tri_padded_pairs) and not to fpad; launch_warp_batch writes the batch:
+// candidates st->wt[0..3] interleaved (float4) and wt[4] to fpad.
 // Vd (device, may be null): its swap selects the layout (solver_pad); the
 // bounding box is recorded in the same frame.
 // f0h: the halo copy of the reference CT (float); mean and U in storage type dt.
 // oc: occupancy bricks of the written volumes (oc.mask null: none).
 cudaError_t launch_warp_pca(const float* f0h, const void* mean, const void* U, int dt, int K, WSrc w,
-                            Grid g, const View* Vd, float* fpad, int* box, Occ oc, cudaStream_t s);
+                            Grid g, const View* Vd, float* fpad, float2* fpair, int* box, Occ oc, cudaStream_t s);
 cudaError_t launch_warp_batch(const float* f0h, const void* mean, const void* U, int dt, int K,
                               const SolveState* st, Grid g, const View* Vd, float4* fpad4, float* fpad,
                               Occ oc, cudaStream_t s);
@@ -627,8 +627,9 @@ cudaError_t launch_drr_siddon(const float* f, const SidView& V, float* p, cudaSt
 // hbatch / use_h: inside a device-driven solve the batch projector sets this
 // conditional handle to whether another candidate batch follows.  oc: the
 // occupancy bricks the warp kernels marked for these volumes (oc.mask null:
-// every ray keeps its box-clipped range).
-cudaError_t launch_drr_solver(const float* fpad, const float4* fpad4, Grid g,
+// every ray keeps its box-clipped range).  Mode 0 reads the x pairs fpair
+// when T.chunk1 is 0 (the march through L1) and fpad when it stages chunks.
+cudaError_t launch_drr_solver(const float* fpad, const float2* fpair, const float4* fpad4, Grid g,
                               const View& Vh, const View* Vd, const float* y, float* pbuf, int mode,
                               SolveState* st, double* part, const Tune& T, unsigned long long hbatch,
                               int use_h, Occ oc, cudaStream_t s);

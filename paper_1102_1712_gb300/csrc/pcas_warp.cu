@@ -147,14 +147,17 @@ __device__ __forceinline__ OccFrame occ_frame(const Occ& oc, const Grid& g, int 
     return o;
 }
 
-// Fused DVF synthesis + warp into the zero-halo layout used by the solver;
-// marks the occupancy bricks of its non-zero voxels.
+// Fused DVF synthesis + warp into the zero-halo layout used by the solver
+// (fpad), or into its x-pair copy (fpair not null: each voxel stored as the
+// first value of its own pair and the second of the pair before it; the
+// pairs' halo values stay the zeros the caller wrote); marks the occupancy
+// bricks of its non-zero voxels.
 // VEC: 4 voxels per thread along x (nx % 4 == 0, 16-byte aligned model).
 template <bool VEC, typename T>
 __global__ void __launch_bounds__(kWarpThreads)
 k_warp_pca(const float* __restrict__ f0h, const T* __restrict__ mean,
            const T* __restrict__ U, int K, WSrc ws, Grid g, const View* __restrict__ Vp,
-           float* __restrict__ fpad, int* __restrict__ box_out, Occ occ) {
+           float* __restrict__ fpad, float2* __restrict__ fpair, int* __restrict__ box_out, Occ occ) {
     if (ws.phase && *ws.phase >= PH_STOP) return;
     const int swp = Vp ? Vp->swap : 0;
     const Pad pd = solver_pad(g.nx, g.ny, g.nz, swp);
@@ -195,7 +198,23 @@ k_warp_pca(const float* __restrict__ f0h, const T* __restrict__ mean,
                 if (swp) occ_mark(oc.m, oc.gen, oc.nbx, oc.nby, j, j, i + e0, i + e1, k);
                 else occ_mark(oc.m, oc.gen, oc.nbx, oc.nby, i + e0, i + e1, j, j, k);
             }
-            if (swp) {
+            if (fpair) {                    // voxel d is .x of pair d and .y of pair d - 1
+                float* p = reinterpret_cast<float*>(fpair);
+                if (swp) {
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        const long d = pad_index(pd, j, i + e, k);
+                        p[2 * d - 1] = o[e];
+                        p[2 * d] = o[e];
+                    }
+                } else {                    // d a multiple of 4: floats 2d - 1 ... 2d + 6
+                    const long d = pad_index(pd, i, j, k);
+                    p[2 * d - 1] = o[0];
+                    *reinterpret_cast<float4*>(p + 2 * d) = make_float4(o[0], o[1], o[1], o[2]);
+                    *reinterpret_cast<float2*>(p + 2 * d + 4) = make_float2(o[2], o[3]);
+                    p[2 * d + 6] = o[3];
+                }
+            } else if (swp) {
 #pragma unroll
                 for (int e = 0; e < 4; e++) fpad[pad_index(pd, j, i + e, k)] = o[e];
             } else {
@@ -219,7 +238,14 @@ k_warp_pca(const float* __restrict__ f0h, const T* __restrict__ mean,
                 box_add(b, a0, a1, k);
                 if (oc.m) occ_mark(oc.m, oc.gen, oc.nbx, oc.nby, a0, a0, a1, a1, k);
             }
-            fpad[pad_index(pd, a0, a1, k)] = o;
+            const long d = pad_index(pd, a0, a1, k);
+            if (fpair) {
+                float* p = reinterpret_cast<float*>(fpair);
+                p[2 * d - 1] = o;
+                p[2 * d] = o;
+            } else {
+                fpad[d] = o;
+            }
         }
     }
     box_reduce(b, box_out);
@@ -366,14 +392,14 @@ cudaError_t pca_dvf_t(const void* mean, const void* U, int K, const float* w, Gr
 
 template <typename T>
 cudaError_t warp_pca_t(const float* f, const void* mean, const void* U, int K, WSrc w, Grid g,
-                       const View* Vd, float* fpad, int* box, Occ oc, cudaStream_t s) {
+                       const View* Vd, float* fpad, float2* fpair, int* box, Occ oc, cudaStream_t s) {
     const unsigned a = sizeof(T) * 4;
-    bool vec = (g.nx % 4 == 0) && aligned(mean, a) && aligned(U, a) && aligned(fpad, 16);
+    bool vec = (g.nx % 4 == 0) && aligned(mean, a) && aligned(U, a) && aligned(fpad, 16) && aligned(fpair, 16);
     const T* m = static_cast<const T*>(mean);
     const T* u = static_cast<const T*>(U);
     const RowLaunch L = row_launch(g, vec ? 4 : 1);
-    if (vec) k_warp_pca<true, T><<<L.grid, L.threads, 0, s>>>(f, m, u, K, w, g, Vd, fpad, box, oc);
-    else k_warp_pca<false, T><<<L.grid, L.threads, 0, s>>>(f, m, u, K, w, g, Vd, fpad, box, oc);
+    if (vec) k_warp_pca<true, T><<<L.grid, L.threads, 0, s>>>(f, m, u, K, w, g, Vd, fpad, fpair, box, oc);
+    else k_warp_pca<false, T><<<L.grid, L.threads, 0, s>>>(f, m, u, K, w, g, Vd, fpad, fpair, box, oc);
     return cudaGetLastError();
 }
 
@@ -423,8 +449,8 @@ cudaError_t launch_fill_f0h(const void* f0, int dt, Grid g, float* f0h, unsigned
 }
 
 cudaError_t launch_warp_pca(const float* f0, const void* mean, const void* U, int dt, int K, WSrc w,
-                            Grid g, const View* Vd, float* fpad, int* box, Occ oc, cudaStream_t s) {
-    PCAS_DT_DISPATCH(dt, (warp_pca_t<T>(f0, mean, U, K, w, g, Vd, fpad, box, oc, s)))
+                            Grid g, const View* Vd, float* fpad, float2* fpair, int* box, Occ oc, cudaStream_t s) {
+    PCAS_DT_DISPATCH(dt, (warp_pca_t<T>(f0, mean, U, K, w, g, Vd, fpad, fpair, box, oc, s)))
 }
 
 cudaError_t launch_warp_batch(const float* f0, const void* mean, const void* U, int dt, int K,

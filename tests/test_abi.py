@@ -64,7 +64,7 @@ def test_workspace_bytes_host_only(lib):
     cap = 32 * 32 * 25 * 256                                 # 8x8x4 tiles of the Jacobian compaction
     f0h = 262 * 262 * 106 * 4                                # reference CT with a three-voxel zero halo
     occ = 33 * 33 * 13 * 4                                   # occupancy bricks of 8^3 voxels
-    need = f0h + occ + npad * (4 + 16) + M * (6 * 4 + 32) + cap * (4 + 4 * 3)   # f (+ 5th candidate), 4 candidates,
+    need = f0h + occ + npad * (4 + 8 + 16) + M * (6 * 4 + 32) + cap * (4 + 4 * 3)   # f (+ 5th), its pairs, 4 cands,
     assert need <= n < need + 2_000_000 and n % 256 == 0       # 6 projections, ray table, compacted voxels
     assert P.workspace_bytes(vol, cb, 0) == 0 and P.workspace_bytes(vol, cb, 9) == 0
     # room for the y-fastest layout too: a non-square grid takes the larger of the two
@@ -185,5 +185,5 @@ def test_tuning_table_host_only(lib):
 
 def test_static_scratch_example_fits(lib):
     """The size the header quotes as fitting the static scratch does fit."""
-    n = P.workspace_bytes(S.volume(80, 80, 40, 4.0, 4.0, 4.0), S.cone_beam(192, 144, 2.0, 2.0), 3)
+    n = P.workspace_bytes(S.volume(72, 72, 40, 4.0, 4.0, 4.0), S.cone_beam(192, 144, 2.0, 2.0), 3)
     assert 0 < n <= 16 * 1024 * 1024
