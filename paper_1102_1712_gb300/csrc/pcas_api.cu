@@ -212,7 +212,7 @@ Layout layout(const pcas_vol* vol, const pcas_cb* cb, int K) {
     L.state = off; off += align256(sizeof(SolveState));
     L.view = off; off += align256(sizeof(View));
     L.f0h = off; off += align256((size_t)f0h_count(vol->nx, vol->ny, vol->nz) * sizeof(float));  // f0, halo 3
-    L.f0m = off; off += align256((size_t)occ_count(vol->nx, vol->ny, vol->nz));     // its bricks (zeroed with it)
+    L.f0m = off; off += align256((size_t)f0b_count(vol->nx, vol->ny, vol->nz));     // its bricks (zeroed with it)
     L.fpad = off; off += align256(npad * sizeof(float));                 // f(w), zero halo
     L.fpair = off; off += align256(npad * sizeof(float2));               // f(w) as x pairs (the L1 march)
     L.fpad4 = off; off += align256(npad * sizeof(float4));               // candidates 0-3 (4 in fpad)

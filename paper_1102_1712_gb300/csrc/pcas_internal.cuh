@@ -120,38 +120,50 @@ struct SolveState {
 enum : int { BOX_EMPTY = 0x3fffffff };
 
 // ------------------------------------------------------ occupancy bricks
-// Empty-space skipping of the solver projectors (exact).  A sample of the
-// march whose cell has its (0,0,0) tap at c = floor(q) (frame voxel indices)
-// belongs to brick ((c_x + 1) >> 3, (c_y + 1) >> 3, (c_z + 1) >> 3), clamped to
-// the grid of (n >> 3) + 1 bricks per axis; its eight taps lie in
-// [8 b - 1, 8 b + 7] per axis.  The warp kernels mark every brick whose taps
+// Empty-space skipping of the solver projectors (exact), on bricks of B^3
+// voxels, B = 1 << OCC_LOG = 4.  A sample of the march whose cell has its
+// (0,0,0) tap at c = floor(q) (frame voxel indices) belongs to brick
+// ((c_x + 1) >> OCC_LOG, ...), clamped to the grid of (n >> OCC_LOG) + 1
+// bricks per axis; its eight taps lie in [B b - 1, B b + B - 1] per axis.
+// (The bricks bound each ray's samples to the span between its first and
+// last occupied brick, so smaller bricks cut the empty samples at the ends
+// of the span: about 8 % of the samples with B = 8, 4 % with B = 4 on the
+// sequence phantom.)  The warp kernels mark every brick whose taps
 // include a non-zero voxel of the volumes they write with the current pass
 // number; the projector that reads those volumes treats a brick holding any
 // other number as empty: each of its samples interpolates eight zero taps and
 // adds exactly +0, so leaving such samples out of a ray changes no bit of the
 // sum.  Marks of earlier passes can only make the projector do more work, so
 // the mask is never cleared; the projector's last block advances the number.
-// The reference CT has bricks of its own (world axes, one byte each, 0 or 1):
-// k_fill_f0h marks them when it writes the halo copy, and the warp and
-// Jacobian kernels interpolate only in cells of marked bricks -- elsewhere all
-// eight taps are zero and so is the result (A.5) and its gradient (A.8).
+// The reference CT has bricks of its own (8^3 voxels, world axes, one byte
+// each, 0 or 1; f0b_n): k_fill_f0h marks them when it writes the halo copy,
+// and the warp and Jacobian kernels interpolate only in cells of marked
+// bricks -- elsewhere all eight taps are zero and so is the result (A.5) and
+// its gradient (A.8).
 struct Occ {
     unsigned int* mask;       // null: no marking and no skipping
     unsigned int* gen;        // the pass number (SolveState::occ_gen)
     const unsigned char* f0m; // bricks of the reference CT (null: none)
 };
-__host__ __device__ inline int occ_n(int n) { return (n >> 3) + 1; }
+constexpr int OCC_LOG = 2;
+__host__ __device__ inline int occ_n(int n) { return (n >> OCC_LOG) + 1; }
 __host__ __device__ inline long occ_count(int nx, int ny, int nz) {
     return (long)occ_n(nx) * occ_n(ny) * occ_n(nz);
 }
+// Bricks of the reference CT (8^3 voxels).
+__host__ __device__ inline int f0b_n(int n) { return (n >> 3) + 1; }
+__host__ __device__ inline long f0b_count(int nx, int ny, int nz) {
+    return (long)f0b_n(nx) * f0b_n(ny) * f0b_n(nz);
+}
 // Marks the bricks whose taps include a frame voxel of [x0, x1] x [y0, y1] x
-// {z}: voxel v is a tap of the cells of bricks v >> 3 and (v + 1) >> 3 along
-// each axis (two bricks where v + 1 is a multiple of 8).
+// {z}: voxel v is a tap of the cells of bricks v >> OCC_LOG and
+// (v + 1) >> OCC_LOG along each axis (two bricks where v + 1 is a multiple
+// of B).
 __device__ __forceinline__ void occ_mark(unsigned int* m, unsigned int gen, int nbx, int nby, int x0, int x1,
                                          int y0, int y1, int z) {
-    for (int bz = z >> 3; bz <= (z + 1) >> 3; bz++)
-        for (int by = y0 >> 3; by <= (y1 + 1) >> 3; by++)
-            for (int bx = x0 >> 3; bx <= (x1 + 1) >> 3; bx++) m[((long)bz * nby + by) * nbx + bx] = gen;
+    for (int bz = z >> OCC_LOG; bz <= (z + 1) >> OCC_LOG; bz++)
+        for (int by = y0 >> OCC_LOG; by <= (y1 + 1) >> OCC_LOG; by++)
+            for (int bx = x0 >> OCC_LOG; bx <= (x1 + 1) >> OCC_LOG; bx++) m[((long)bz * nby + by) * nbx + bx] = gen;
 }
 
 // Number of the next (up to TRIAL_BATCH) step sizes mu, beta mu, ... that the
@@ -302,7 +314,7 @@ __device__ __forceinline__ int f0_brick(const Grid& g, float qx, float qy, float
     qx = fminf(fmaxf(qx, -2.0f), (float)g.nx + 1.0f);
     qy = fminf(fmaxf(qy, -2.0f), (float)g.ny + 1.0f);
     qz = fminf(fmaxf(qz, -2.0f), (float)g.nz + 1.0f);
-    const int nbx = occ_n(g.nx), nby = occ_n(g.ny), nbz = occ_n(g.nz);
+    const int nbx = f0b_n(g.nx), nby = f0b_n(g.ny), nbz = f0b_n(g.nz);
     const int bx = min(max(((int)floorf(qx) + 1) >> 3, 0), nbx - 1);
     const int by = min(max(((int)floorf(qy) + 1) >> 3, 0), nby - 1);
     const int bz = min(max(((int)floorf(qz) + 1) >> 3, 0), nbz - 1);
@@ -327,7 +339,7 @@ __device__ __forceinline__ float tri_halo(const float* __restrict__ f, const Gri
 // spanning more than two bricks along an axis is reported live.
 __device__ __forceinline__ bool f0_box_live(const unsigned char* __restrict__ m, const Grid& g, float lox,
                                             float loy, float loz, float hix, float hiy, float hiz) {
-    const int nbx = occ_n(g.nx), nby = occ_n(g.ny), nbz = occ_n(g.nz);
+    const int nbx = f0b_n(g.nx), nby = f0b_n(g.ny), nbz = f0b_n(g.nz);
     auto br = [](float q, int n, int nb) {
         q = fminf(fmaxf(q, -2.0f), (float)n + 1.0f);
         return min(max(((int)floorf(q) + 1) >> 3, 0), nb - 1);

@@ -112,7 +112,7 @@ k_fill_f0h(const T* __restrict__ f0, Grid g, float* __restrict__ f0h, unsigned c
            const int* __restrict__ skip) {
     if (skip && *skip) return;
     const long sy = g.nx + 2 * F0_HALO, sz = sy * (g.ny + 2 * F0_HALO);
-    const int nbx = occ_n(g.nx), nby = occ_n(g.ny);
+    const int nbx = f0b_n(g.nx), nby = f0b_n(g.ny);
     const int rows = g.ny * g.nz;
     for (int r = blockIdx.x; r < rows; r += gridDim.x) {
         const int j = r % g.ny, k = r / g.ny;

@@ -1,4 +1,4 @@
-"""Empty-space skipping of the solver projectors (occupancy bricks of 8^3
+"""Empty-space skipping of the solver projectors (occupancy bricks of 4^3
 voxels marked by the warp kernels): exact by construction, so every result
 with skipping on equals the result with it off bit for bit -- costs and
 gradients, host-driven and device-driven solves, both volume layouts, rays
@@ -74,7 +74,7 @@ def test_solves_equal_with_and_without_skipping(P, angle):
 
 def _long_problem():
     """A 400-voxel-long box of air with a small object at its far end (from a
-    source at +x) and one off to the side: rays at 90 deg cross about fifty
+    source at +x) and one off to the side: rays at 90 deg cross about a hundred
     empty bricks before the object, more than a walk takes, and many rays
     miss the object entirely."""
     vol = S.volume(400, 24, 16, 1.0, 1.0, 1.0)
