@@ -210,8 +210,9 @@ int localize_tumor(const float* mean, const float* U, int K, const double* w,
  *   owned by the caller and must stay valid until destroy; cb gives the
  *   detector shape (its angle and offsets are per-solve); params are fixed.
  *   Allocates pinned host staging buffers, a stream for the localisations
- *   of runs, and builds the graph; not for use inside stream capture.
- *   pcas_solver_destroy waits for that stream before it frees them.
+ *   of runs and one for the uploads of their host images, and builds the
+ *   graph; not for use inside stream capture.  pcas_solver_destroy waits for
+ *   those streams before it frees them.
  * pcas_solver_solve: y (device, [nv][nu]) is copied into the solver's image
  *   buffer unless it is that buffer (pcas_solver_y_buffer) or NULL; the view
  *   is the creation view with this angle and these detector offsets.
@@ -267,7 +268,10 @@ int pcas_solver_fix_view(pcas_solver solver, double angle_rad, void* cache, size
  *   0).  Synchronous.
  * pcas_solver_seq_enqueue: queues one projection on the stream and returns
  *   its ticket.  y: [nv][nu] floats, device or (pinned) host memory, copied
- *   into the solver's buffer; the view is the creation view at angle_rad.
+ *   into the solver's buffer; a host image is uploaded on a stream the solver
+ *   owns, beside the solves queued before it (keep it unchanged until the
+ *   ticket's result has been read); the view is the creation view at
+ *   angle_rad.
  *   The start is w_first (host, K doubles, NULL = zeros) while the run has
  *   no solution yet, then the latest solution while it has fewer than L,
  *   then the Eq. (3) prediction from the last L (the same arithmetic as

@@ -1475,6 +1475,14 @@ struct pcas_solver_s {
     cudaEvent_t ev[SEQ_RING];   // a slot is free again once its launch passed this
     cudaEvent_t ev_solved[SEQ_RING];  // a run's solve of the slot is done (localisation may start)
     cudaStream_t loc_stream;          // localisations of a run's projections
+    // host images of a run: uploaded on the copy stream into one of two
+    // staging buffers (device, in the workspace) while earlier projections
+    // solve, then copied device to device into y ahead of their own solve
+    float* ystage[2];
+    cudaStream_t cp_stream;
+    cudaEvent_t ev_cp[2];             // the upload into ystage[b] is done
+    cudaEvent_t ev_used[2];           // the solve stream has copied ystage[b] out
+    int ynext;
     long long next;       // tickets handed out (slot = ticket % SEQ_RING)
     long long seq_first;  // first ticket of the current run (-1: no run)
     long long slot_ticket[SEQ_RING];  // ticket of a run's projection in each slot (-1: none)
@@ -1504,8 +1512,9 @@ struct pcas_batch_s {
 namespace {
 
 size_t solver_extra(const pcas_cb* cb) {
-    return align256((size_t)cb->nu * cb->nv * sizeof(float)) + align256(sizeof(Stage)) + align256(sizeof(SeqBlock)) +
-           align256(SEQ_RING * sizeof(SeqOut));
+    const size_t img = align256((size_t)cb->nu * cb->nv * sizeof(float));
+    return img + align256(sizeof(Stage)) + align256(sizeof(SeqBlock)) + align256(SEQ_RING * sizeof(SeqOut)) +
+           2 * img;                       // the image, ..., and two staging images of a run
 }
 
 // Captures one device-driven solve into `graph` as an independent branch
@@ -1666,9 +1675,17 @@ void solver_free(pcas_solver s) {
         cudaStreamSynchronize(s->loc_stream);
         cudaStreamDestroy(s->loc_stream);
     }
+    if (s->cp_stream) {
+        cudaStreamSynchronize(s->cp_stream);
+        cudaStreamDestroy(s->cp_stream);
+    }
     for (int i = 0; i < SEQ_RING; i++) {
         if (s->ev[i]) cudaEventDestroy(s->ev[i]);
         if (s->ev_solved[i]) cudaEventDestroy(s->ev_solved[i]);
+    }
+    for (int b = 0; b < 2; b++) {
+        if (s->ev_cp[b]) cudaEventDestroy(s->ev_cp[b]);
+        if (s->ev_used[b]) cudaEventDestroy(s->ev_used[b]);
     }
     if (s->h_ring) cudaFreeHost(s->h_ring);
     if (s->h_out) cudaFreeHost(s->h_out);
@@ -1720,6 +1737,11 @@ int pcas_solver_create(pcas_solver* out, const void* f0, const void* mean, const
     s->d_seq = reinterpret_cast<SeqBlock*>(extra + off);
     off += align256(sizeof(SeqBlock));
     s->d_out = reinterpret_cast<SeqOut*>(extra + off);
+    off += align256(SEQ_RING * sizeof(SeqOut));
+    for (int b = 0; b < 2; b++) {
+        s->ystage[b] = reinterpret_cast<float*>(extra + off);
+        off += align256((size_t)cb->nu * cb->nv * sizeof(float));
+    }
     s->W.view = &s->d_stage->v;           // the kernels read the staged view
     s->seq_first = -1;
     for (int i = 0; i < SEQ_RING; i++) s->slot_ticket[i] = -1;
@@ -1735,6 +1757,11 @@ int pcas_solver_create(pcas_solver* out, const void* f0, const void* mean, const
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_solved[i], cudaEventDisableTiming);
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->loc_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cp_stream, cudaStreamNonBlocking);
+    for (int b = 0; b < 2 && e == cudaSuccess; b++) {
+        e = cudaEventCreateWithFlags(&s->ev_cp[b], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_used[b], cudaEventDisableTiming);
+    }
     // zero the halos once: the warp kernels never write them
     if (e == cudaSuccess) e = cudaMemsetAsync(s->W.fpad, 0, s->W.fpad_bytes + s->W.fpad4_bytes, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->W.f0h, 0, s->W.f0h_bytes, st);
@@ -1928,8 +1955,27 @@ int pcas_solver_seq_enqueue(pcas_solver s, const void* y, double angle_rad, cons
     cudaStream_t st = as_stream(stream);
     int slot;
     PCAS_TRY(solver_stage(s, angle_rad, s->cb.off_u, s->cb.off_v, w_first, 1, &slot, st));
-    const size_t M = (size_t)s->cb.nu * s->cb.nv;
-    if (y && y != s->y) PCAS_CUDA(cudaMemcpyAsync(s->y, y, M * sizeof(float), cudaMemcpyDefault, st));
+    const size_t bytes = (size_t)s->cb.nu * s->cb.nv * sizeof(float);
+    if (y && y != s->y) {
+        cudaPointerAttributes pa{};
+        const bool host = cudaPointerGetAttributes(&pa, y) == cudaSuccess &&
+                          (pa.type == cudaMemoryTypeHost || pa.type == cudaMemoryTypeUnregistered);
+        cudaGetLastError();               // a failed query leaves no error behind
+        if (host) {
+            // the upload runs on the copy stream beside the projections
+            // queued before this one; this solve waits only for its own image
+            const int b = s->ynext;
+            s->ynext ^= 1;
+            PCAS_CUDA(cudaStreamWaitEvent(s->cp_stream, s->ev_used[b], 0));
+            PCAS_CUDA(cudaMemcpyAsync(s->ystage[b], y, bytes, cudaMemcpyHostToDevice, s->cp_stream));
+            PCAS_CUDA(cudaEventRecord(s->ev_cp[b], s->cp_stream));
+            PCAS_CUDA(cudaStreamWaitEvent(st, s->ev_cp[b], 0));
+            PCAS_CUDA(cudaMemcpyAsync(s->y, s->ystage[b], bytes, cudaMemcpyDeviceToDevice, st));
+            PCAS_CUDA(cudaEventRecord(s->ev_used[b], st));
+        } else {
+            PCAS_CUDA(cudaMemcpyAsync(s->y, y, bytes, cudaMemcpyDefault, st));
+        }
+    }
     PCAS_CUDA(cudaGraphLaunch(s->exec, st));
     // the localisation and the result record on the solver's own stream, so
     // that the next projection's solve does not wait for them
