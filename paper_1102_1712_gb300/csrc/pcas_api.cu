@@ -285,6 +285,16 @@ inline Occ occ_of(const Ws& W, const Tune& T) {
 // projector marches through L1 (chunk1 = 0), else the scalar volume it stages.
 inline float2* pair_of(const Ws& W, const Tune& T) { return T.chunk1 == 0 ? W.fpair : nullptr; }
 
+// The first evaluation's warp of a solve at the staged w (st->w), fused with
+// the Jacobian pass of the gradient at that w (launch_warp_jac): the next
+// launch_adjoint_grad with T.vt skips its own.
+inline cudaError_t first_warp(const Ws& W, const Tune& T, const Grid& g, const void* mean, const void* U, int dt,
+                              int K, cudaStream_t s) {
+    const Occ oc = occ_of(W, T);
+    const JacWarp jw{W.view, W.fpad, pair_of(W, T), W.st->box[0], oc};
+    return launch_warp_jac(g, W.f0h, oc.f0m, mean, U, dt, K, W.st, W.adj, T.vt, jw, s);
+}
+
 // ------------------------------------------------------------ launch shapes
 // Default shapes: 8 x 4 warp patches, 16-sample chunks for the batch
 // projector (the one-volume projector marches through L1), 8 x 8 x 4 voxel tiles,
@@ -463,6 +473,7 @@ __global__ void k_init_state(SolveState* st, int K, double w0, double w1, double
     st->cur = 0; st->phase = PH_RUNNING; st->evals = 0; st->trials = 0;
     st->nvalid = 0; st->iters = 0; st->batches = 0; st->max_iter = max_iter; st->launches = 0;
     st->wide = 1;
+    st->jac_ready = 0;
     for (int i = 0; i < 4; i++) st->counter[i] = 0u;
     for (int i = 0; i < 2; i++)
         for (int j = 0; j < 6; j++) st->box[i][j] = BOX_EMPTY;
@@ -522,12 +533,8 @@ int stage_f0h(const void* f0, int dt, const Grid& g, const Ws& W, const Tune& T,
 int eval_gradient_pipeline(const void* f0, const void* mean, const void* U, int dt, int K, const float* y,
                            const Grid& g, const View& V, const Ws& W, int step_setup, const Tune& T,
                            cudaStream_t s) {
-    WSrc ws{};
-    ws.dev = W.st->w;
-    ws.phase = &W.st->phase;
     PCAS_TRY(stage_f0h(f0, dt, g, W, T, s));
-    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(W.f0h, mean, U, dt, K, ws, g, W.view, W.fpad, pair_of(W, T), W.st->box[0],
-                                                    occ_of(W, T), s));
+    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, first_warp(W, T, g, mean, U, dt, K, s));
     PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
                 launch_drr_solver(W.fpad, W.fpair, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, T, 0ull, 0,
                                   occ_of(W, T), s));
@@ -552,12 +559,8 @@ int solve_host(const void* f0, const void* mean, const void* U, int dtype, int K
     PCAS_CUDA(cudaMemsetAsync(W.fpad, 0, W.fpad_bytes + W.fpad4_bytes, s));   // zero halos
     PCAS_TRY(launch_init(W.st, K, w_init, prm, s));
     PCAS_TRY(upload_view(W.view, V, s));
-    WSrc wcur{};
-    wcur.dev = W.st->w;
-    wcur.phase = &W.st->phase;
     PCAS_TRY(stage_f0h(f0, dtype, g, W, T, s));
-    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(W.f0h, mean, U, dtype, K, wcur, g, W.view, W.fpad, pair_of(W, T),
-                                                    W.st->box[0], occ_of(W, T), s));
+    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, first_warp(W, T, g, mean, U, dtype, K, s));
     PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
                 launch_drr_solver(W.fpad, W.fpair, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, T, 0ull, 0,
                                   occ_of(W, T), s));
@@ -813,8 +816,11 @@ int cost_grad_f0(const float* f0, const float* mean, const float* U, int K, cons
     wsrc.dev = W.st->w;
     wsrc.phase = &W.st->phase;
     PCAS_TRY(stage_f0h(f0, DT_F32, g, W, T, s));
-    PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(W.f0h, mean, U, DT_F32, K, wsrc, g, W.view, W.fpad, pair_of(W, T),
-                                                    W.st->box[0], occ_of(W, T), s));
+    if (dJdw)       // the gradient at w follows: its Jacobian pass comes with the warp
+        PCAS_LAUNCH(PCAS_K_WARP_PCA, s, first_warp(W, T, g, mean, U, DT_F32, K, s));
+    else
+        PCAS_LAUNCH(PCAS_K_WARP_PCA, s, launch_warp_pca(W.f0h, mean, U, DT_F32, K, wsrc, g, W.view, W.fpad,
+                                                        pair_of(W, T), W.st->box[0], occ_of(W, T), s));
     PCAS_LAUNCH(PCAS_K_DRR_SOLVER, s,
                 launch_drr_solver(W.fpad, W.fpair, W.fpad4, g, V, W.view, y, W.pbuf, 0, W.st, W.part_drr, T, 0ull, 0,
                                   occ_of(W, T), s));
@@ -1080,9 +1086,12 @@ int pcas_autotune(const void* f0, const void* mean, const void* U, int dtype, in
     if (rc == PCAS_OK) {
         const int vts[NVOXTILE] = {0, 1, 2, 3, 4, 5}, gs[3] = {4, 8, 16};
         const int ka[1] = {PCAS_K_ADJ_GRAD};
+        // the voxel tile also shapes the first evaluation's warp, which does
+        // the first gradient's Jacobian pass
+        const int kv[2] = {PCAS_K_WARP_PCA, PCAS_K_ADJ_GRAD};
         const int bins2[2] = {0, 4};
         int c = best.vt;
-        rc = sweep([](Tune& X, int v) { X.vt = v; }, vts, NVOXTILE, ka, 1, probe, 4, &c);
+        rc = sweep([](Tune& X, int v) { X.vt = v; }, vts, NVOXTILE, kv, 2, probe, 4, &c);
         best.vt = c;
         int g = best.adj_mult;
         if (rc == PCAS_OK) rc = sweep([](Tune& X, int v) { X.adj_mult = v; }, gs, 3, ka, 1, bins2, 2, &g);
@@ -1364,6 +1373,7 @@ __global__ void k_init_dev(SolveState* st, const InitBlock* __restrict__ ib, con
     st->cur = 0; st->phase = PH_RUNNING; st->evals = 0; st->trials = 0;
     st->nvalid = 0; st->iters = 0; st->batches = 0; st->launches = 1;
     st->wide = 1;
+    st->jac_ready = 0;
     for (int i = 0; i < 4; i++) st->counter[i] = 0u;
     for (int i = 0; i < 2; i++)
         for (int j = 0; j < 6; j++) st->box[i][j] = BOX_EMPTY;
@@ -1556,11 +1566,7 @@ int capture_solve(pcas_solver s, cudaGraph_t graph, cudaStream_t cs, const float
     // the reference CT is copied for every solve, except after the first
     // projection of a run (k_init_dev sets keep_f0h then)
     PCAS_G(launch_fill_f0h(s->f0, s->dtype, g, W.f0h, s->tune.skip ? W.f0m : nullptr, &W.st->keep_f0h, cs));
-    WSrc wcur{};
-    wcur.dev = W.st->w;
-    wcur.phase = &W.st->phase;
-    PCAS_G(launch_warp_pca(W.f0h, s->mean, s->U, s->dtype, s->K, wcur, g, W.view, W.fpad, pair_of(W, s->tune),
-                           W.st->box[0], oc, cs));
+    PCAS_G(first_warp(W, s->tune, g, s->mean, s->U, s->dtype, s->K, cs));
     PCAS_G(launch_drr_solver(W.fpad, W.fpair, W.fpad4, g, V, W.view, s->y, W.pbuf, 0, W.st, W.part_drr, s->tune, 0ull, 0,
                              oc, cs));
     k_ctrl_start<<<1, 1, 0, cs>>>(W.st, s->h_outer);

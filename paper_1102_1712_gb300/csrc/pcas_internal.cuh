@@ -115,6 +115,8 @@ struct SolveState {
     int box[2][6];
     unsigned int occ_gen;                 // pass number of the occupancy bricks (never reset)
     int keep_f0h;                         // device-driven run: the halo copy of f0 is current
+    int jac_ready;                        // the first evaluation's warp did the next gradient's
+                                          // Jacobian pass (launch_warp_jac); its gather clears it
 };
 
 enum : int { BOX_EMPTY = 0x3fffffff };
@@ -154,6 +156,18 @@ __host__ __device__ inline long occ_count(int nx, int ny, int nz) {
 __host__ __device__ inline int f0b_n(int n) { return (n >> 3) + 1; }
 __host__ __device__ inline long f0b_count(int nx, int ny, int nz) {
     return (long)f0b_n(nx) * f0b_n(ny) * f0b_n(nz);
+}
+// Occupancy bricks of the solver frame (see Occ): the frame exchanges x and y
+// when swp is set.
+struct OccFrame {
+    unsigned int* m;
+    unsigned int gen;
+    int nbx, nby;
+};
+__device__ __forceinline__ OccFrame occ_frame(const Occ& oc, int nx, int ny, int swp) {
+    OccFrame o{oc.mask, 0u, occ_n(swp ? ny : nx), occ_n(swp ? nx : ny)};
+    if (oc.mask) o.gen = *oc.gen;
+    return o;
 }
 // Marks the bricks whose taps include a frame voxel of [x0, x1] x [y0, y1] x
 // {z}: voxel v is a tap of the cells of bricks v >> OCC_LOG and
@@ -658,6 +672,23 @@ struct AdjScratch {
     int* tile_count;    // ntiles
     int* tile_off;      // ntiles + 1
 };
+// The first evaluation's warp fused with the Jacobian pass of the gradient at
+// the same w: one read of the motion model gives f(w), written as
+// launch_warp_pca writes it (fpad, or its x-pair copy fpair when not null;
+// bounding box into box, occupancy bricks of the output in occ), and the
+// compacted voxels of the gradient pass in voxel tile vt, as its Jacobian pass
+// writes them; the next launch_adjoint_grad (same vt) then skips its Jacobian
+// pass (SolveState::jac_ready).  view: its swap selects the layout.
+struct JacWarp {
+    const View* view;
+    float* fpad;
+    float2* fpair;
+    int* box;
+    Occ occ;
+};
+cudaError_t launch_warp_jac(Grid g, const float* f0h, const unsigned char* f0m, const void* mean, const void* U,
+                            int dt, int K, SolveState* st, const AdjScratch& as, int vt, const JacWarp& jw,
+                            cudaStream_t s);
 // hbatch / use_h: inside a device-driven solve the gradient's last block opens
 // (or not) the iteration's candidate-batch loop by setting this handle.
 // join (may be null): an event the gather waits for (the residual pass, which

@@ -134,19 +134,6 @@ k_fill_f0h(const T* __restrict__ f0, Grid g, float* __restrict__ f0h, unsigned c
     }
 }
 
-// Occupancy bricks of the solver frame (see Occ): the frame exchanges x and y
-// when swp is set.
-struct OccFrame {
-    unsigned int* m;
-    unsigned int gen;
-    int nbx, nby;
-};
-__device__ __forceinline__ OccFrame occ_frame(const Occ& oc, const Grid& g, int swp) {
-    OccFrame o{oc.mask, 0u, occ_n(swp ? g.ny : g.nx), occ_n(swp ? g.nx : g.ny)};
-    if (oc.mask) o.gen = *oc.gen;
-    return o;
-}
-
 // Fused DVF synthesis + warp into the zero-halo layout used by the solver
 // (fpad), or into its x-pair copy (fpair not null: each voxel stored as the
 // first value of its own pair and the second of the pair before it; the
@@ -161,7 +148,7 @@ k_warp_pca(const float* __restrict__ f0h, const T* __restrict__ mean,
     if (ws.phase && *ws.phase >= PH_STOP) return;
     const int swp = Vp ? Vp->swap : 0;
     const Pad pd = solver_pad(g.nx, g.ny, g.nz, swp);
-    const OccFrame oc = occ_frame(occ, g, swp);
+    const OccFrame oc = occ_frame(occ, g.nx, g.ny, swp);
     __shared__ float s_w[PCAS_KMAX];
     if (threadIdx.x < PCAS_KMAX) {
         float wv = 0.f;                     // static indices keep ws out of local memory
@@ -269,7 +256,7 @@ k_warp_batch(const float* __restrict__ f0h, const T* __restrict__ mean,
     if (st->phase >= PH_STOP || st->nvalid < 1) return;    // same gate as the batch projector
     const int swp = Vp ? Vp->swap : 0;
     const Pad pd = solver_pad(g.nx, g.ny, g.nz, swp);
-    const OccFrame oc = occ_frame(occ, g, swp);
+    const OccFrame oc = occ_frame(occ, g.nx, g.ny, swp);
     __shared__ float s_w[TRIAL_BATCH][KT];
     if (threadIdx.x < TRIAL_BATCH * KT) {
         const int j = threadIdx.x / KT, k = threadIdx.x % KT;
