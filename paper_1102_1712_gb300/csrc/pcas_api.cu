@@ -281,9 +281,9 @@ inline Occ occ_of(const Ws& W, const Tune& T) {
     return Occ{T.skip ? W.occ : nullptr, &W.st->occ_gen, T.skip ? W.f0m : nullptr};
 }
 
-// Where the one-volume warp writes f(w): the x-pair copy when the one-volume
-// projector marches through L1 (chunk1 = 0), else the scalar volume it stages.
-inline float2* pair_of(const Ws& W, const Tune& T) { return T.chunk1 == 0 ? W.fpair : nullptr; }
+// Where the one-volume warp writes f(w): its x-pair copy, which the one-volume
+// projector reads (through L1, or staged chunk by chunk).
+inline float2* pair_of(const Ws& W, const Tune&) { return W.fpair; }
 
 // The first evaluation's warp of a solve at the staged w (st->w), fused with
 // the Jacobian pass of the gradient at that w (launch_warp_jac): the next
