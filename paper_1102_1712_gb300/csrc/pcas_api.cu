@@ -218,7 +218,7 @@ Layout layout(const pcas_vol* vol, const pcas_cb* cb, int K) {
     L.fpad4 = off; off += align256(npad * sizeof(float4));               // candidates 0-3 (4 in fpad)
     L.occ = off; off += align256((size_t)occ_count(vol->nx, vol->ny, vol->nz) * sizeof(unsigned int));
     L.pbuf = off; off += align256((size_t)NBUF * M * sizeof(float));     // projection ring
-    L.rayt = off; off += align256(2 * M * sizeof(float4));               // (step, r), (1/step, 0)
+    L.rayt = off; off += align256(2 * M * sizeof(float4) + M * sizeof(float));   // (step, r), (1/step, 0); r
     L.part_drr = off; off += align256((size_t)drr_blocks(cb->nu, cb->nv) * DRR_PART_VALS * sizeof(double));
     L.part_res = off; off += align256((size_t)resid_blocks(cb->nu, cb->nv) * sizeof(double));
     L.part_adj = off; off += align256((size_t)ADJ_MAX_BLOCKS * PCAS_KMAX * sizeof(double));

@@ -64,7 +64,7 @@ def test_workspace_bytes_host_only(lib):
     cap = 32 * 32 * 25 * 256                                 # 8x8x4 tiles of the Jacobian compaction
     f0h = 262 * 262 * 106 * 4                                # reference CT with a three-voxel zero halo
     occ = 65 * 65 * 26 * 4 + 33 * 33 * 13                   # bricks: 4^3 of the solver volumes, 8^3 of f0
-    need = f0h + occ + npad * (4 + 8 + 16) + M * (6 * 4 + 32) + cap * (4 + 4 * 3)   # f (+ 5th), its pairs, 4 cands,
+    need = f0h + occ + npad * (4 + 8 + 16) + M * (6 * 4 + 36) + cap * (4 + 4 * 3)   # f (+ 5th), its pairs, 4 cands,
     assert need <= n < need + 2_000_000 and n % 256 == 0       # 6 projections, ray table, compacted voxels
     assert P.workspace_bytes(vol, cb, 0) == 0 and P.workspace_bytes(vol, cb, 9) == 0
     # room for the y-fastest layout too: a non-square grid takes the larger of the two
