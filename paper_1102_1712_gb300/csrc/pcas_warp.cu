@@ -263,12 +263,11 @@ k_warp_batch(const float* __restrict__ f0h, const T* __restrict__ mean,
         s_w[j][k] = (float)st->wt[j][k];
     }
     __syncthreads();
-    float wk[TRIAL_BATCH][KT];
-#pragma unroll
-    for (int b = 0; b < TRIAL_BATCH; b++)
-#pragma unroll
-        for (int kk = 0; kk < KT; kk++) wk[b][kk] = s_w[b][kk];
-    int bx[6] = {BOX_EMPTY, BOX_EMPTY, BOX_EMPTY, BOX_EMPTY, BOX_EMPTY, BOX_EMPTY};
+    // read from shared memory at each use (broadcast), not kept in registers
+    const volatile float(*wk)[KT] = s_w;
+    // the block's voxels share j and k: of the output's bounding box only the
+    // x extent varies within it
+    int ilo = BOX_EMPTY, ihi = BOX_EMPTY;     // min i, min -i of the non-zero voxels
     const int j = blockIdx.y, k = blockIdx.z;
     const long N = (long)g.nx * g.ny * g.nz;
     // VPT voxels per thread, blockDim.x apart (each pass of the loop stores
@@ -295,9 +294,11 @@ k_warp_batch(const float* __restrict__ f0h, const T* __restrict__ mean,
 #pragma unroll
             for (int kk = 0; kk < KT; kk++)      // Eq. (1) in the order of the single-volume warp
 #pragma unroll
-                for (int c = 0; c < 3; c++)
+                for (int b = 0; b < TRIAL_BATCH; b++) {
+                    const float wbk = wk[b][kk];
 #pragma unroll
-                    for (int b = 0; b < TRIAL_BATCH; b++) x[b][c] = fmaf(wk[b][kk], u[kk][c], x[b][c]);
+                    for (int c = 0; c < 3; c++) x[b][c] = fmaf(wbk, u[kk][c], x[b][c]);
+                }
             float q[TRIAL_BATCH][3];
 #pragma unroll
             for (int b = 0; b < TRIAL_BATCH; b++) {
@@ -337,10 +338,16 @@ k_warp_batch(const float* __restrict__ f0h, const T* __restrict__ mean,
             fpad4[d] = make_float4(o[0], o[1], o[2], o[3]);
             fpad[d] = o[4];
             if (o[0] != 0.0f || o[1] != 0.0f || o[2] != 0.0f || o[3] != 0.0f || o[4] != 0.0f) {
-                box_add(bx, a0, a1, k);
+                ilo = min(ilo, i);
+                ihi = min(ihi, -i);
                 if (oc.m) occ_mark(oc.m, oc.gen, oc.nbx, oc.nby, a0, a0, a1, a1, k);
             }
         }
+    }
+    int bx[6] = {BOX_EMPTY, BOX_EMPTY, BOX_EMPTY, BOX_EMPTY, BOX_EMPTY, BOX_EMPTY};
+    if (ilo != BOX_EMPTY) {       // in the frame: (i, j) or, swapped, (j, i)
+        bx[0] = swp ? j : ilo; bx[1] = swp ? ilo : j; bx[2] = k;
+        bx[3] = swp ? -j : ihi; bx[4] = swp ? ihi : -j; bx[5] = -k;
     }
     box_reduce(bx, box_out);      // every thread of the block, one call site
 }
