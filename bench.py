@@ -323,11 +323,41 @@ KERNEL_FILE = {"warp_pca": "k_warp_jac", "warp_batch": "k_warp_batch", "drr_solv
 KERNEL_SOURCES = {"warp_batch": ("pcas_warp.cu", "pcas_internal.cuh")}
 
 
+def strip_comments(src):
+    """C++ source with its comments removed and each run of white space
+    collapsed to one blank, so that a change to comments or layout alone
+    leaves the hash of a kernel's sources as it was."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+            out.append(" ")
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def kernel_source_hash(kernel):
+    """Hash of the code (comments and layout aside) of the files a kernel is
+    built from; a profile summary records it when its counters are taken."""
     import hashlib
     h = hashlib.sha256()
     for f in KERNEL_SOURCES.get(kernel, ("pcas_project.cu", "pcas_internal.cuh")):
-        h.update(open(os.path.join(ROOT, "paper_1102_1712_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_1102_1712_gb300", "csrc", f), encoding="utf-8").read()
+        h.update(strip_comments(src).encode())
     return h.hexdigest()[:16]
 
 
