@@ -373,8 +373,10 @@ typedef struct {
  * projector's width and chunk, the voxel tile and the gather size, each
  * chosen by the time of the kernels it drives (about 150 trial solves); a
  * shape replaces the one in place (default or earlier choice) only when it
- * is more than 1.5 % faster, so that timing noise does not flip choices
- * (which can change the rounding of results) between runs.  f0, mean, U, y,
+ * is more than 1.5 % faster, and among the shapes within 1.5 % of the
+ * fastest the first in a fixed candidate order is taken, so that timing
+ * noise does not flip choices (which can change the rounding of results)
+ * between runs.  f0, mean, U, y,
  * ws: device, as solve_projection
  * (ws of pcas_workspace_bytes); w_init: host, K doubles or NULL (zeros);
  * out (host, may be NULL) receives the stored entry.  Synchronous.  Bins

@@ -982,14 +982,18 @@ int pcas_autotune(const void* f0, const void* mean, const void* U, int dtype, in
     for (int b = 0; b < NBIN; b++) ok_bin[b] = true;
     const int probe[4] = {0, 2, 4, 6};
     // A shape replaces the one in place (the default, or the choice of an
-    // earlier step) only when it is faster by more than this margin: choices
-    // that timing noise would flip from run to run -- and with them, through
-    // the order of the projectors' and the gradient's sums, the rounding of
-    // the results -- stay put.
+    // earlier step) only when it is faster by more than this margin, and
+    // among the shapes within the margin of the fastest the first in the
+    // candidate list's order is taken: choices that timing noise would flip
+    // from run to run -- and with them, through the order of the projectors'
+    // and the gradient's sums, the rounding of the results -- stay put.
     const double keep = 0.985;
     auto sweep = [&](auto apply, const int* cands, int ncand, const int* kinds, int nkinds, const int* bins,
                      int nbins, int* choice) -> int {
-        double bestt = 0.0, inct = -1.0;
+        constexpr int kMaxCand = 8;
+        if (ncand > kMaxCand) return fail(PCAS_ERR_INVALID_ARG, "autotune: too many candidates");
+        double bestt = 0.0, inct = -1.0, tc[kMaxCand];
+        bool any = false;
         const int inc = *choice;
         for (int c = 0; c < ncand; c++) {
             Tune X = best;
@@ -1004,13 +1008,15 @@ int pcas_autotune(const void* f0, const void* mean, const void* U, int dtype, in
                 for (int k = 0; k < nkinds; k++) t += a[kinds[k]];
                 used++;
             }
+            tc[c] = used ? t : -1.0;
             if (used && cands[c] == inc) inct = t;
-            if (used && (c == 0 || t < bestt)) {
-                bestt = t;
-                *choice = cands[c];
-            }
+            if (used && (!any || t < bestt)) bestt = t;
+            any = any || used;
         }
-        if (inct > 0.0 && *choice != inc && bestt > keep * inct) *choice = inc;
+        if (!any) return PCAS_OK;
+        if (inct > 0.0 && bestt > keep * inct) return PCAS_OK;      // the incumbent stays
+        for (int c = 0; c < ncand; c++)
+            if (tc[c] > 0.0 && keep * tc[c] <= bestt) { *choice = cands[c]; break; }
         return PCAS_OK;
     };
     // 0. empty-space skipping, timed over the warps (which mark the bricks) and
@@ -1039,33 +1045,38 @@ int pcas_autotune(const void* f0, const void* mean, const void* U, int dtype, in
         const int cur = best.swap[b] ? 1 : 0;
         if (tt[1 - cur] < keep * tt[cur]) best.swap[b] = (unsigned char)(1 - cur);
     }
-    // 2. per angle bin, the patch width and chunk of the batch projector
+    // 2. per angle bin, the patch width and chunk of the batch projector (the
+    //    same rule: the incumbent, else the first within the margin)
     for (int b = 0; b < NBIN && rc == PCAS_OK; b++) {
         if (!ok_bin[b]) continue;
-        double bestt = 0.0, inct = -1.0;
+        const int chunks[3] = {12, 16, 24};
+        double bestt = 0.0, inct = -1.0, tc[3][3];
         const int ilw = best.lw4[b], ich = best.chunk4[b];
-        int blw = ilw, bch = ich;
-        bool first = true;
+        bool any = false;
         for (int lw = 2; lw <= 4 && rc == PCAS_OK; lw++) {
-            const int chunks[3] = {12, 16, 24};
             for (int c = 0; c < 3 && rc == PCAS_OK; c++) {
+                tc[lw - 2][c] = -1.0;
                 Tune X = best;
                 X.lw4[b] = (unsigned char)lw;
                 X.chunk4[b] = (unsigned char)chunks[c];
                 rc = tr.run(X, b, a);
                 if (rc != PCAS_OK || a[PCAS_K_DRR_BATCH] <= 0.0) continue;
-                if (lw == ilw && chunks[c] == ich) inct = a[PCAS_K_DRR_BATCH];
-                if (first || a[PCAS_K_DRR_BATCH] < bestt) {
-                    bestt = a[PCAS_K_DRR_BATCH];
-                    blw = lw;
-                    bch = chunks[c];
-                    first = false;
-                }
+                const double t = a[PCAS_K_DRR_BATCH];
+                tc[lw - 2][c] = t;
+                if (lw == ilw && chunks[c] == ich) inct = t;
+                if (!any || t < bestt) bestt = t;
+                any = true;
             }
         }
-        if (inct > 0.0 && bestt > keep * inct) { blw = ilw; bch = ich; }
-        best.lw4[b] = (unsigned char)blw;
-        best.chunk4[b] = (unsigned char)bch;
+        if (rc != PCAS_OK || !any || (inct > 0.0 && bestt > keep * inct)) continue;
+        bool set = false;
+        for (int lw = 2; lw <= 4 && !set; lw++)
+            for (int c = 0; c < 3 && !set; c++)
+                if (tc[lw - 2][c] > 0.0 && keep * tc[lw - 2][c] <= bestt) {
+                    best.lw4[b] = (unsigned char)lw;
+                    best.chunk4[b] = (unsigned char)chunks[c];
+                    set = true;
+                }
     }
     // 3. patch width and chunk of the one-volume projector (0: it reads through L1)
     if (rc == PCAS_OK) {
