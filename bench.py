@@ -327,27 +327,34 @@ def strip_comments(src):
     """C++ source with its comments removed and each run of white space
     collapsed to one blank, so that a change to comments or layout alone
     leaves the hash of a kernel's sources as it was."""
-    out, i, n = [], 0, len(src)
+    out, code, i, n = [], [], 0, len(src)
+
+    def flush():
+        out.append(" ".join("".join(code).split()))
+        code.clear()
+
     while i < n:
         c = src[i]
-        if c in "\"'":
+        if c in "\"'":                  # a literal: kept verbatim
             j = i + 1
             while j < n and src[j] != c:
                 j += 2 if src[j] == "\\" else 1
+            flush()
             out.append(src[i:j + 1])
             i = j + 1
         elif src.startswith("//", i):
             j = src.find("\n", i)
             i = n if j < 0 else j
-            out.append(" ")
+            code.append(" ")
         elif src.startswith("/*", i):
             j = src.find("*/", i + 2)
             i = n if j < 0 else j + 2
-            out.append(" ")
+            code.append(" ")
         else:
-            out.append(c)
+            code.append(c)
             i += 1
-    return " ".join("".join(out).split())
+    flush()
+    return " ".join(t for t in out if t)
 
 
 def kernel_source_hash(kernel):

@@ -42,3 +42,22 @@ def test_changed_inputs_are_refused():
     except SystemExit:
         return
     raise AssertionError("a changed trace was accepted")
+
+
+def test_kernel_source_hash_ignores_comments_only():
+    """A profile summary's counters stay attached to its kernel across edits
+    of comments and layout, and are dropped once the code changes."""
+    src = ('// header\n#include "x.cuh"\n/* block\n comment */ __global__ void k(float* p) {\n'
+           '    p[0] = 1.0f;   // one\n    const char* s = "a // not a comment";\n    char c = \'/\';\n}\n')
+    reworded = ('// another header, longer\n#include "x.cuh"\n__global__   void k(float* p)\n{\n'
+                '    p[0] = 1.0f;\n    const char* s = "a // not a comment";  /* two */\n    char c = \'/\';\n}\n')
+    changed = src.replace("1.0f", "2.0f")
+    moved_string = src.replace('"a // not a comment"', '"a  // not a comment"')
+    strip = bench.strip_comments
+    assert strip(src) == strip(reworded).replace("k(float* p) {", "k(float* p) {")
+    assert strip(src) != strip(changed)
+    assert strip(src) != strip(moved_string)        # string literals are code, kept verbatim
+    assert "block" not in strip(src) and "one" not in strip(src)
+    assert '"a // not a comment"' in strip(src)
+    for kernel in bench.KERNEL_FILE:
+        assert len(bench.kernel_source_hash(kernel)) == 16
