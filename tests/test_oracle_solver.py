@@ -178,6 +178,35 @@ def test_localize_linear_field_closed_form():
     np.testing.assert_allclose(c, np.linalg.solve(np.eye(3) + A, c_ref), atol=1e-9)
 
 
+def test_localize_smooth_field_solves_the_fixed_point_equation():
+    """A smooth random motion (three eigenvector fields, w ~ O(1)): the
+    returned point satisfies c + x(c) = c_ref, with x(c) evaluated
+    independently by scipy's linear interpolation of the field (zero outside
+    the grid), and agrees with a general root finder started elsewhere."""
+    nd = pytest.importorskip("scipy.ndimage")
+    opt = pytest.importorskip("scipy.optimize")
+    vol = S.volume(40, 36, 28, 3.0, 3.0, 3.0)
+    U = S.eigen_dvfs(vol, 3, seed=9).astype(np.float64)
+    w = np.array([0.8, -0.5, 0.3])
+    dvf = np.tensordot(w, U, axes=(0, 0)).reshape(3, 28, 36, 40)     # mm, [c][z][y][x]
+    o = np.array([vol["ox"], vol["oy"], vol["oz"]])
+    s = np.array([vol["sx"], vol["sy"], vol["sz"]])
+
+    def x_of(c):
+        q = (np.asarray(c) - o) / s                                      # voxel index (x, y, z)
+        coords = np.array([[q[2]], [q[1]], [q[0]]])
+        return np.array([nd.map_coordinates(dvf[k], coords, order=1, mode="constant", cval=0.0)[0]
+                         for k in range(3)])
+
+    for c_ref in (np.array([6.0, -4.0, 3.0]), np.array([-15.0, 10.0, -8.0])):
+        c, ok = O.localize_tumor(None, U, w, vol, c_ref, max_iter=500, tol_mm=1e-12)
+        assert ok
+        assert np.abs(c + x_of(c) - c_ref).max() <= 1e-9
+        sol = opt.root(lambda v: v + x_of(v) - c_ref, c_ref + 2.0, method="hybr", tol=1e-13)
+        assert sol.success
+        np.testing.assert_allclose(c, sol.x, atol=1e-7)
+
+
 def test_localize_reports_non_convergence():
     vol = S.volume(24, 22, 20, 3.0, 3.0, 3.0)
     U = S.eigen_dvfs(vol, 1, seed=4)
